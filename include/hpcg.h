@@ -1,0 +1,207 @@
+/*
+ * hpcg.h -- C ABI of the GB300 (sm_103a) multigrid-preconditioned CG library
+ * for the HPCG 27-point operator, following Scolari & Yzelman, "Effective
+ * implementation of the High Performance Conjugate Gradient benchmark on
+ * GraphBLAS" (arXiv 2304.08232).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid rows are numbered i = x + nx*(y + ny*z) (x fastest); every vector
+ *    argument is a dense array of one value per row in that order.
+ *  - Pointers named *_dev are DEVICE pointers on the handle's GPU; pointers
+ *    named *_host are host pointers.  The caller owns every buffer it passes
+ *    and keeps it alive until the stream has finished the call's work.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous with respect to the host unless stated otherwise.
+ *  - Every call returns an hpcg_status; HPCG_OK == 0.  A non-zero status
+ *    leaves caller buffers in an unspecified state unless stated otherwise.
+ *    hpcg_strerror() turns a status into text.
+ *  - The operator is matrix-free: diagonal 26 (+ kappa_i when a diagonal field
+ *    is bound), -1 to every other grid point within distance one in each
+ *    coordinate (Dirichlet boundary, no ghost rows), Sections II-B and II-C.
+ *  - Colour classes (Section III-A, greedy colouring, eight colours on this
+ *    grid) are color_i = (x&1) + 2(y&1) + 4(z&1); coarse level l+1 has each
+ *    dimension halved and coarse row c = (xc,yc,zc) is injected from fine row
+ *    (2xc, 2yc, 2zc) (Section II-E, straight injection).
+ */
+#ifndef HPCG_GB300_H
+#define HPCG_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hpcg_ctx *hpcg_handle;
+
+typedef enum {
+  HPCG_OK = 0,
+  HPCG_ERR_INVALID_ARG = 1,   /* null pointer, bad level, dimension < 2 or not divisible by 2^(levels-1) */
+  HPCG_ERR_CUDA = 2,          /* a CUDA runtime call failed; the text is in hpcg_last_cuda_error() */
+  HPCG_ERR_BREAKDOWN = 3,     /* CG breakdown: p.Ap <= 0, or a NaN/Inf scalar */
+  HPCG_ERR_NOT_CONVERGED = 4, /* tolerance not met within max_iters; x and stats are still valid */
+  HPCG_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out; the kernel returned early */
+  HPCG_ERR_NO_WORKSPACE = 6,  /* bound workspace smaller than hpcg_workspace_bytes() */
+  HPCG_ERR_OUT_OF_MEMORY = 7, /* cudaMalloc of an internally owned workspace failed */
+  HPCG_ERR_UNSUPPORTED = 8    /* the call does not apply to this handle's kind */
+} hpcg_status;
+
+typedef enum {
+  HPCG_FP64 = 0,  /* every step in FP64 */
+  HPCG_MIXED = 1  /* MG preconditioner in FP32 (operator values -1 and 26 are exact
+                     in BF16 and are compile-time constants of the matrix-free
+                     kernels; a kappa diagonal is kept in FP32); the outer residual,
+                     dot products and solution update stay in FP64 */
+} hpcg_precision;
+
+typedef struct {
+  int nx, ny, nz;   /* finest grid */
+  int levels;       /* MG levels including the finest, 1..8 (Listing 1; HPCG uses 4) */
+  int precision;    /* hpcg_precision of the preconditioner */
+  int pre_sweeps;   /* smoother applications before the coarse correction (default 1) */
+  int post_sweeps;  /* smoother applications after it (default 1) */
+  int symmetric;    /* 1: forward colours 0..7 then backward 7..0 (default); 0: forward only */
+  int check_every;  /* tolerance solves: host looks at the device convergence flag every
+                       this many iterations (default 1; work after convergence is skipped
+                       on the device, so a larger value only costs idle launches) */
+  int max_rhs;      /* largest nrhs of hpcg_pcg_solve_multi the workspace is sized for (default 0) */
+} hpcg_options;
+
+typedef struct {
+  int iters;          /* CG iterations run */
+  int restarts;       /* residual replacements r = b - A x (mixed precision) */
+  int converged;      /* 1 if ||r||/||r0|| <= rel_tol was reached */
+  int status;         /* hpcg_status of the solve */
+  double rel_res;     /* final recurrence residual ||r_k||/||r_0|| */
+  double *history;    /* host, caller-owned, may be NULL: ||r_k||/||r_0|| for k = 1..iters */
+  int history_cap;    /* capacity of history in doubles */
+} hpcg_stats;
+
+/* Fills *opt with defaults for an nx x ny x nz grid with 4 levels, FP64. */
+int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz);
+
+/* Builds a hierarchy handle (Section II-B input generation, Listing 1 levels).
+ * Allocates no device memory: bind a workspace (below) or let the first compute
+ * call allocate one it owns.  Errors: INVALID_ARG for null out, levels outside
+ * 1..8, a dimension < 2 on the coarsest level or not divisible by 2^(levels-1). */
+int hpcg_setup(int nx, int ny, int nz, int levels, hpcg_handle *out);
+
+/* As hpcg_setup with explicit options.  kappa_dev (nullable, device, n doubles)
+ * is a per-row diagonal field: A_ii = 26 + kappa_i; the values are copied into
+ * the workspace on the first compute call (or by hpcg_set_kappa), coarse levels
+ * take kappa at their injected fine rows. */
+int hpcg_setup_ex(const hpcg_options *opt, const double *kappa_dev, hpcg_handle *out);
+
+/* Replaces the diagonal field (device, n doubles; NULL removes it).  Needs a
+ * workspace; runs on `stream`. */
+int hpcg_set_kappa(hpcg_handle h, const double *kappa_dev, void *stream);
+
+/* Frees the handle and any workspace it allocated itself (not a bound one).
+ * Synchronises the device first. */
+int hpcg_destroy(hpcg_handle h);
+
+/* Bytes of device workspace the handle needs (all levels' vectors, CG vectors,
+ * reduction partials, device scalars, residual history). */
+int hpcg_workspace_bytes(hpcg_handle h, size_t *bytes);
+
+/* Binds caller-owned device memory (>= hpcg_workspace_bytes, 256-byte aligned)
+ * as the workspace; the library then allocates nothing.  The memory must stay
+ * valid until hpcg_destroy or another bind.  Errors: NO_WORKSPACE if too small. */
+int hpcg_bind_workspace(hpcg_handle h, void *dev, size_t bytes);
+
+/* Dimensions of MG level `level` (0 = finest) into dims_host[3]. */
+int hpcg_level_dims(hpcg_handle h, int level, int *dims_host);
+
+/* --- setup maps, written by GPU kernels into caller device buffers --------- */
+/* Colour of every row of `level` (Section III-A), int32 [n_level]. */
+int hpcg_get_colors(hpcg_handle h, int level, int *colors_dev, void *stream);
+/* Injection map of `level` -> level+1: f2c[c] = fine row of coarse row c,
+ * int32 [n_{level+1}] (Section II-E). INVALID_ARG on the coarsest level. */
+int hpcg_get_f2c(hpcg_handle h, int level, int *f2c_dev, void *stream);
+/* Nonzeros of every row (8..27), int32 [n_level] (Section II-C). */
+int hpcg_get_row_nnz(hpcg_handle h, int level, int *nnz_dev, void *stream);
+/* HPCG right-hand side b = A * ones (exact solution ones), FP64 [n_0]. */
+int hpcg_get_rhs(hpcg_handle h, double *b_dev, void *stream);
+
+/* --- single steps of the hot path -------------------------------------------- */
+/* y = A_level x (spmv, Section II-C); FP64 [n_level]; x and y must not overlap. */
+int hpcg_spmv(hpcg_handle h, int level, const double *x_dev, double *y_dev, void *stream);
+
+/* One colour step of the red-black Gauss-Seidel pass (Listings 2 and 3): every
+ * row i of colour `color` gets z_i <- (r_i - sum_{j != i} A_ij z_j) / A_ii, in
+ * place on z; FP64 [n_level]. */
+int hpcg_rbgs_color(hpcg_handle h, int level, int color, const double *r_dev, double *z_dev, void *stream);
+
+/* One smoother application on `level`: colours 0..7, then (symmetric option)
+ * 7..0, in place on z (the smoother that replaces SGS, Sections II-D, III-A). */
+int hpcg_rbgs(hpcg_handle h, int level, const double *r_dev, double *z_dev, void *stream);
+
+/* Fused residual and restriction (Listing 1 lines 5-6, Section II-E):
+ * rc[c] = r[f2c[c]] - (A_level z)[f2c[c]]; r, z FP64 [n_level], rc [n_{level+1}]. */
+int hpcg_restrict_residual(hpcg_handle h, int level, const double *r_dev, const double *z_dev, double *rc_dev, void *stream);
+
+/* Refinement and correction (Listing 1 line 9): z[f2c[c]] += zc[c]; others unchanged. */
+int hpcg_prolong_add(hpcg_handle h, int level, const double *zc_dev, double *z_dev, void *stream);
+
+/* z = M r: one V-cycle of Listing 1 from z = 0 on all levels, in the handle's
+ * precision; FP64 [n_0] in and out; r and z must not overlap. */
+int hpcg_mg_vcycle(hpcg_handle h, const double *r_dev, double *z_dev, void *stream);
+
+/* out_dev[0] = a . b over n FP64 values, deterministic fixed-order reduction. */
+int hpcg_dot(hpcg_handle h, long n, const double *a_dev, const double *b_dev, double *out_dev, void *stream);
+
+/* w = alpha x + beta y over n FP64 values (waxpby, Section II-C); w may alias x or y. */
+int hpcg_waxpby(hpcg_handle h, long n, double alpha, const double *x_dev, double beta, const double *y_dev, double *w_dev, void *stream);
+
+/* --- solves -------------------------------------------------------------------- */
+/* Preconditioned CG (Section II-C) with the MG preconditioner, HPCG iteration
+ * order.  x_dev holds x0 on entry and the solution on exit.  rel_tol <= 0 runs
+ * exactly max_iters iterations; otherwise stops once ||r_k||/||r_0|| <= rel_tol.
+ * Mixed precision replaces r by b - A x in FP64 when the residual stalls for 3
+ * iterations.  Blocks the host until the solve is done (it reads back the
+ * statistics); stats (nullable) is filled.  Returns NOT_CONVERGED (x valid) if
+ * rel_tol > 0 was not reached, BREAKDOWN if p.Ap <= 0 or NaN. */
+int hpcg_pcg_solve(hpcg_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol,
+                   hpcg_stats *stats, void *stream);
+
+/* Backward of the differentiable solve x = A(kappa)^{-1} b: solves the adjoint
+ * A lambda = grad_x (A is symmetric) with the same MG-PCG from lambda = 0, then
+ * grad_b = lambda and, if grad_kappa_dev is not NULL, grad_kappa_i = -lambda_i x_i
+ * (the diagonal of -lambda x^T, since dA/dkappa_i = e_i e_i^T).  All FP64 [n_0].
+ * grad_b_dev receives lambda and must not alias x_dev or grad_x_dev. */
+int hpcg_pcg_backward(hpcg_handle h, const double *x_dev, const double *grad_x_dev, double *grad_b_dev,
+                      double *grad_kappa_dev, int max_iters, double rel_tol, hpcg_stats *stats, void *stream);
+
+/* --- batched forms -------------------------------------------------------------- */
+/* nrhs right-hand sides on the handle's grid in one multi-RHS solve; B and X are
+ * FP64 [nrhs][n_0] (each RHS contiguous); X holds the initial guesses.  Every
+ * RHS stops on its own at rel_tol (its updates are frozen after convergence).
+ * stats (nullable) is an array of nrhs records.  nrhs in 1..64. */
+int hpcg_pcg_solve_multi(hpcg_handle h, int nrhs, const double *B_dev, double *X_dev, int max_iters,
+                         double rel_tol, hpcg_stats *stats, void *stream);
+
+/* A batch of `count` independent grids (dims_host: 3*count ints, nx ny nz per
+ * instance), each with its own `levels`-level hierarchy, solved together.
+ * Vectors of the batch are the instances' vectors concatenated in order. */
+int hpcg_setup_batch(int count, const int *dims_host, int levels, int precision, hpcg_handle *out);
+
+/* Row offset of every instance in the concatenated vectors, int64 [count+1]. */
+int hpcg_batch_offsets(hpcg_handle h, long *offsets_host);
+
+/* Solves every instance of a batch handle; b, x concatenated FP64; stats
+ * (nullable) is an array of `count` records.  Each instance stops on its own. */
+int hpcg_pcg_solve_batch(hpcg_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol,
+                         hpcg_stats *stats, void *stream);
+
+/* --- diagnostics ------------------------------------------------------------------ */
+const char *hpcg_strerror(int status);
+/* Text of the last CUDA error seen by the library in this process (thread-unsafe). */
+const char *hpcg_last_cuda_error(void);
+/* Number of kernel launches the library has issued in this process. */
+long hpcg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPCG_GB300_H */

@@ -1,0 +1,98 @@
+"""ctypes declarations of the C ABI in include/hpcg.h.
+
+Loading fails loudly (ImportError) when the CUDA library has not been built:
+there is no CPU fallback anywhere in this package.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_l = ctypes.c_long
+_d = ctypes.c_double
+
+
+class hpcg_options(ctypes.Structure):
+    _fields_ = [("nx", _i), ("ny", _i), ("nz", _i), ("levels", _i), ("precision", _i), ("pre_sweeps", _i),
+                ("post_sweeps", _i), ("symmetric", _i), ("check_every", _i), ("max_rhs", _i)]
+
+
+class hpcg_stats(ctypes.Structure):
+    _fields_ = [("iters", _i), ("restarts", _i), ("converged", _i), ("status", _i), ("rel_res", _d),
+                ("history", ctypes.POINTER(_d)), ("history_cap", _i)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "hpcg_options_default": (_i, [ctypes.POINTER(hpcg_options), _i, _i, _i]),
+    "hpcg_setup": (_i, [_i, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "hpcg_setup_ex": (_i, [ctypes.POINTER(hpcg_options), _vp, ctypes.POINTER(_vp)]),
+    "hpcg_set_kappa": (_i, [_vp, _vp, _vp]),
+    "hpcg_destroy": (_i, [_vp]),
+    "hpcg_workspace_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "hpcg_bind_workspace": (_i, [_vp, _vp, ctypes.c_size_t]),
+    "hpcg_level_dims": (_i, [_vp, _i, ctypes.POINTER(_i)]),
+    "hpcg_get_colors": (_i, [_vp, _i, _vp, _vp]),
+    "hpcg_get_f2c": (_i, [_vp, _i, _vp, _vp]),
+    "hpcg_get_row_nnz": (_i, [_vp, _i, _vp, _vp]),
+    "hpcg_get_rhs": (_i, [_vp, _vp, _vp]),
+    "hpcg_spmv": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_rbgs_color": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "hpcg_rbgs": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_restrict_residual": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "hpcg_prolong_add": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_mg_vcycle": (_i, [_vp, _vp, _vp, _vp]),
+    "hpcg_dot": (_i, [_vp, _l, _vp, _vp, _vp, _vp]),
+    "hpcg_waxpby": (_i, [_vp, _l, _d, _vp, _d, _vp, _vp, _vp]),
+    "hpcg_pcg_solve": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
+    "hpcg_pcg_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
+    "hpcg_pcg_solve_multi": (_i, [_vp, _i, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
+    "hpcg_setup_batch": (_i, [_i, ctypes.POINTER(_i), _i, _i, ctypes.POINTER(_vp)]),
+    "hpcg_batch_offsets": (_i, [_vp, ctypes.POINTER(_l)]),
+    "hpcg_pcg_solve_batch": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
+    "hpcg_strerror": (ctypes.c_char_p, [_i]),
+    "hpcg_last_cuda_error": (ctypes.c_char_p, []),
+    "hpcg_launch_count": (_l, []),
+}
+
+HPCG_OK = 0
+HPCG_ERR_NOT_CONVERGED = 4
+FP64, MIXED = 0, 1
+
+_LIB = None
+
+
+def load(path=None):
+    """Loads the built library (no build here); raises ImportError if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.lib_path()
+    if not os.path.exists(path):
+        raise ImportError("CUDA library %s is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class HpcgError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        msg = lib.hpcg_strerror(status).decode()
+        if status == 2:
+            msg += " (" + lib.hpcg_last_cuda_error().decode() + ")"
+        super().__init__("%s: %s [status %d]" % (where, msg, status))
+        self.status = status
+
+
+def check(status, where, allow=()):
+    if status != HPCG_OK and status not in allow:
+        raise HpcgError(status, where)
+    return status

@@ -1,0 +1,294 @@
+"""Thin torch-facing wrappers with the names of the C ABI (include/hpcg.h)."""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import check, hpcg_options, hpcg_stats
+
+_f64 = torch.float64
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t, n, dtype=_f64, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be contiguous %s with %d elements" % (name, dtype, n))
+    return t
+
+
+def launch_count():
+    return _lib.load().hpcg_launch_count()
+
+
+class _Stats:
+    """Host-side statistics of one solve (iterations, residual history)."""
+
+    def __init__(self, st, hist):
+        self.iters = st.iters
+        self.restarts = st.restarts
+        self.converged = bool(st.converged)
+        self.status = st.status
+        self.rel_res = st.rel_res
+        self.history = hist[: st.iters].tolist() if hist is not None else []
+
+    def __repr__(self):
+        return "Stats(iters=%d, rel_res=%.3e, converged=%s, restarts=%d)" % (
+            self.iters, self.rel_res, self.converged, self.restarts)
+
+
+def _new_stats(cap):
+    import numpy as np
+    hist = np.zeros(max(cap, 1), dtype=np.float64)
+    st = hpcg_stats()
+    st.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st.history_cap = len(hist)
+    return st, hist
+
+
+class HpcgProblem:
+    """One grid hierarchy (hpcg_setup_ex) with a torch-allocated workspace."""
+
+    def __init__(self, nx, ny, nz, levels=4, precision="fp64", kappa=None, pre_sweeps=1, post_sweeps=1,
+                 symmetric=True, max_rhs=0, check_every=1, device=None):
+        self.lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("HpcgProblem needs a CUDA device")
+        self.device = torch.device(device or "cuda")
+        opt = hpcg_options()
+        check(self.lib.hpcg_options_default(ctypes.byref(opt), nx, ny, nz), "hpcg_options_default")
+        opt.levels = levels
+        opt.precision = {"fp64": _lib.FP64, "mixed": _lib.MIXED}[precision]
+        opt.pre_sweeps, opt.post_sweeps = pre_sweeps, post_sweeps
+        opt.symmetric = 1 if symmetric else 0
+        opt.max_rhs = max_rhs
+        opt.check_every = check_every
+        self.dims = (nx, ny, nz)
+        self.levels = levels
+        self.precision = precision
+        self.n = nx * ny * nz
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.hpcg_setup_ex(ctypes.byref(opt), None, ctypes.byref(h)), "hpcg_setup_ex")
+            self.h = h
+            nbytes = ctypes.c_size_t()
+            check(self.lib.hpcg_workspace_bytes(self.h, ctypes.byref(nbytes)), "hpcg_workspace_bytes")
+            self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            aligned = (base + 255) & ~255
+            check(self.lib.hpcg_bind_workspace(self.h, ctypes.c_void_p(aligned), nbytes.value), "hpcg_bind_workspace")
+            if kappa is not None:
+                self.set_kappa(kappa)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.lib.hpcg_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    # -- geometry / maps --------------------------------------------------------
+    def level_dims(self, level):
+        d = (ctypes.c_int * 3)()
+        check(self.lib.hpcg_level_dims(self.h, level, d), "hpcg_level_dims")
+        return tuple(d)
+
+    def level_n(self, level):
+        a, b, c = self.level_dims(level)
+        return a * b * c
+
+    def set_kappa(self, kappa):
+        if kappa is not None:
+            kappa = _need(kappa, self.n, name="kappa")
+        check(self.lib.hpcg_set_kappa(self.h, _ptr(kappa), _stream()), "hpcg_set_kappa")
+        self._kappa_ref = kappa
+
+    def get_colors(self, level=0):
+        out = torch.empty(self.level_n(level), dtype=torch.int32, device=self.device)
+        check(self.lib.hpcg_get_colors(self.h, level, _ptr(out), _stream()), "hpcg_get_colors")
+        return out
+
+    def get_f2c(self, level=0):
+        out = torch.empty(self.level_n(level + 1), dtype=torch.int32, device=self.device)
+        check(self.lib.hpcg_get_f2c(self.h, level, _ptr(out), _stream()), "hpcg_get_f2c")
+        return out
+
+    def get_row_nnz(self, level=0):
+        out = torch.empty(self.level_n(level), dtype=torch.int32, device=self.device)
+        check(self.lib.hpcg_get_row_nnz(self.h, level, _ptr(out), _stream()), "hpcg_get_row_nnz")
+        return out
+
+    def get_rhs(self):
+        out = torch.empty(self.n, dtype=_f64, device=self.device)
+        check(self.lib.hpcg_get_rhs(self.h, _ptr(out), _stream()), "hpcg_get_rhs")
+        return out
+
+    # -- single steps -----------------------------------------------------------------
+    def spmv(self, x, level=0, out=None):
+        n = self.level_n(level)
+        _need(x, n, name="x")
+        out = torch.empty_like(x) if out is None else _need(out, n, name="out")
+        check(self.lib.hpcg_spmv(self.h, level, _ptr(x), _ptr(out), _stream()), "hpcg_spmv")
+        return out
+
+    def rbgs_color(self, r, z, color, level=0):
+        n = self.level_n(level)
+        _need(r, n, name="r"), _need(z, n, name="z")
+        check(self.lib.hpcg_rbgs_color(self.h, level, color, _ptr(r), _ptr(z), _stream()), "hpcg_rbgs_color")
+        return z
+
+    def rbgs(self, r, z, level=0):
+        n = self.level_n(level)
+        _need(r, n, name="r"), _need(z, n, name="z")
+        check(self.lib.hpcg_rbgs(self.h, level, _ptr(r), _ptr(z), _stream()), "hpcg_rbgs")
+        return z
+
+    def restrict_residual(self, r, z, level=0, out=None):
+        n = self.level_n(level)
+        _need(r, n, name="r"), _need(z, n, name="z")
+        nc = self.level_n(level + 1)
+        out = torch.empty(nc, dtype=_f64, device=self.device) if out is None else _need(out, nc, name="out")
+        check(self.lib.hpcg_restrict_residual(self.h, level, _ptr(r), _ptr(z), _ptr(out), _stream()),
+              "hpcg_restrict_residual")
+        return out
+
+    def prolong_add(self, zc, z, level=0):
+        _need(zc, self.level_n(level + 1), name="zc"), _need(z, self.level_n(level), name="z")
+        check(self.lib.hpcg_prolong_add(self.h, level, _ptr(zc), _ptr(z), _stream()), "hpcg_prolong_add")
+        return z
+
+    def mg_vcycle(self, r, out=None):
+        _need(r, self.n, name="r")
+        out = torch.empty_like(r) if out is None else _need(out, self.n, name="out")
+        check(self.lib.hpcg_mg_vcycle(self.h, _ptr(r), _ptr(out), _stream()), "hpcg_mg_vcycle")
+        return out
+
+    def dot(self, a, b):
+        out = torch.empty(1, dtype=_f64, device=self.device)
+        check(self.lib.hpcg_dot(self.h, a.numel(), _ptr(a), _ptr(b), _ptr(out), _stream()), "hpcg_dot")
+        return out
+
+    def waxpby(self, alpha, x, beta, y, out=None):
+        out = torch.empty_like(x) if out is None else out
+        check(self.lib.hpcg_waxpby(self.h, x.numel(), alpha, _ptr(x), beta, _ptr(y), _ptr(out), _stream()),
+              "hpcg_waxpby")
+        return out
+
+    # -- solves --------------------------------------------------------------------------
+    def pcg_solve(self, b, x0=None, max_iters=50, tol=0.0, out=None):
+        """Returns (x, stats).  tol <= 0 runs exactly max_iters iterations."""
+        _need(b, self.n, name="b")
+        x = out if out is not None else (x0.clone() if x0 is not None else torch.zeros_like(b))
+        if out is not None and x0 is not None:
+            x.copy_(x0)
+        st, hist = _new_stats(max_iters)
+        rc = self.lib.hpcg_pcg_solve(self.h, _ptr(b), _ptr(x), max_iters, tol, ctypes.byref(st), _stream())
+        check(rc, "hpcg_pcg_solve", allow=(_lib.HPCG_ERR_NOT_CONVERGED,))
+        return x, _Stats(st, hist)
+
+    def pcg_backward(self, x, grad_x, max_iters=200, tol=1e-12, want_kappa=True):
+        _need(x, self.n, name="x"), _need(grad_x, self.n, name="grad_x")
+        gb = torch.empty_like(x)
+        gk = torch.empty_like(x) if want_kappa else None
+        st, hist = _new_stats(max_iters)
+        rc = self.lib.hpcg_pcg_backward(self.h, _ptr(x), _ptr(grad_x), _ptr(gb), _ptr(gk), max_iters, tol,
+                                        ctypes.byref(st), _stream())
+        check(rc, "hpcg_pcg_backward", allow=(_lib.HPCG_ERR_NOT_CONVERGED,))
+        return gb, gk, _Stats(st, hist)
+
+    def pcg_solve_multi(self, B, X0=None, max_iters=50, tol=0.0):
+        nrhs = B.shape[0]
+        _need(B, nrhs * self.n, name="B")
+        X = X0.clone() if X0 is not None else torch.zeros_like(B)
+        sts = (hpcg_stats * nrhs)()
+        hists = []
+        for k in range(nrhs):
+            st, hist = _new_stats(max_iters)
+            sts[k] = st
+            hists.append(hist)
+        rc = self.lib.hpcg_pcg_solve_multi(self.h, nrhs, _ptr(B), _ptr(X), max_iters, tol, sts, _stream())
+        check(rc, "hpcg_pcg_solve_multi", allow=(_lib.HPCG_ERR_NOT_CONVERGED,))
+        return X, [_Stats(sts[k], hists[k]) for k in range(nrhs)]
+
+
+class HpcgBatch:
+    """A batch of independent grids (hpcg_setup_batch), vectors concatenated."""
+
+    def __init__(self, dims, levels=4, precision="fp64", device=None):
+        self.lib = _lib.load()
+        self.device = torch.device(device or "cuda")
+        flat = [int(v) for d in dims for v in d]
+        self.count = len(dims)
+        arr = (ctypes.c_int * len(flat))(*flat)
+        h = ctypes.c_void_p()
+        prec = {"fp64": _lib.FP64, "mixed": _lib.MIXED}[precision]
+        with torch.cuda.device(self.device):
+            check(self.lib.hpcg_setup_batch(self.count, arr, levels, prec, ctypes.byref(h)), "hpcg_setup_batch")
+            self.h = h
+            offs = (ctypes.c_long * (self.count + 1))()
+            check(self.lib.hpcg_batch_offsets(self.h, offs), "hpcg_batch_offsets")
+            self.offsets = list(offs)
+            self.n = self.offsets[-1]
+            nbytes = ctypes.c_size_t()
+            check(self.lib.hpcg_workspace_bytes(self.h, ctypes.byref(nbytes)), "hpcg_workspace_bytes")
+            self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+            aligned = (self.workspace.data_ptr() + 255) & ~255
+            check(self.lib.hpcg_bind_workspace(self.h, ctypes.c_void_p(aligned), nbytes.value), "hpcg_bind_workspace")
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.lib.hpcg_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def pcg_solve(self, b, x0=None, max_iters=200, tol=1e-8):
+        _need(b, self.n, name="b")
+        x = x0.clone() if x0 is not None else torch.zeros_like(b)
+        sts = (hpcg_stats * self.count)()
+        hists = []
+        for k in range(self.count):
+            st, hist = _new_stats(max_iters)
+            sts[k] = st
+            hists.append(hist)
+        rc = self.lib.hpcg_pcg_solve_batch(self.h, _ptr(b), _ptr(x), max_iters, tol, sts, _stream())
+        check(rc, "hpcg_pcg_solve_batch", allow=(_lib.HPCG_ERR_NOT_CONVERGED,))
+        return x, [_Stats(sts[k], hists[k]) for k in range(self.count)]
+
+
+class HpcgSolve(torch.autograd.Function):
+    """x = A(kappa)^{-1} b with a hand-written backward: the adjoint MG-PCG
+    solve lambda = A^{-1} grad_x (A is symmetric), grad_b = lambda and
+    grad_kappa = -lambda * x (hpcg_pcg_backward)."""
+
+    @staticmethod
+    def forward(ctx, b, kappa, problem, max_iters, tol):
+        problem.set_kappa(kappa.detach().contiguous())
+        x, st = problem.pcg_solve(b.detach().contiguous(), max_iters=max_iters, tol=tol)
+        ctx.problem, ctx.max_iters, ctx.tol = problem, max_iters, tol
+        ctx.save_for_backward(x)
+        ctx.forward_stats = st
+        return x
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        (x,) = ctx.saved_tensors
+        gb, gk, _ = ctx.problem.pcg_backward(x, grad_x.contiguous(), max_iters=ctx.max_iters, tol=ctx.tol,
+                                             want_kappa=ctx.needs_input_grad[1])
+        return gb, gk, None, None, None
+
+
+def hpcg_solve(b, kappa, problem, max_iters=200, tol=1e-12):
+    return HpcgSolve.apply(b, kappa, problem, max_iters, tol)

@@ -1,0 +1,849 @@
+// hpcg_core.cu -- host driver of the GB300 MG-PCG library: handle, workspace,
+// V-cycle (Listing 1) and preconditioned CG (Section II-C) enqueueing, CUDA
+// graph capture of one CG iteration, and the C-ABI entry points of hpcg.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "hpcg.h"
+#include "hpcg_kernels.cuh"
+
+using namespace hpcg;
+
+// ---------------------------------------------------------------------------
+// error plumbing
+static char g_last_cuda_error[256] = "no error";
+static std::atomic<long> g_launches{0};
+
+static int cuda_fail(cudaError_t e, const char *what) {
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", what, cudaGetErrorString(e));
+  return HPCG_ERR_CUDA;
+}
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+#define CKL(what)                                         \
+  do {                                                    \
+    g_launches.fetch_add(1, std::memory_order_relaxed);   \
+    cudaError_t e_ = cudaGetLastError();                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);    \
+  } while (0)
+#define TRY(x)              \
+  do {                      \
+    int rc_ = (x);          \
+    if (rc_ != HPCG_OK) return rc_; \
+  } while (0)
+
+static inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------------
+struct LevelData {
+  std::vector<Inst> inst;  // host copy
+  LevelTab tab{};
+  long n = 0;
+  // workspace offsets (bytes)
+  size_t o_tab = 0, o_r = 0, o_z = 0, o_r32 = 0, o_z32 = 0, o_kap = 0, o_invd = 0, o_kap32 = 0, o_invd32 = 0;
+  // device pointers (valid once a workspace is bound)
+  double *r = nullptr, *z = nullptr, *kap = nullptr, *invd = nullptr;
+  float *r32 = nullptr, *z32 = nullptr, *kap32 = nullptr, *invd32 = nullptr;
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  const void *key[4] = {nullptr, nullptr, nullptr, nullptr};
+  long kernels = 0;
+};
+
+struct hpcg_ctx {
+  int batch = 0;  // 0: single grid, 1: batch of grids
+  hpcg_options opt{};
+  int levels = 0;
+  int count = 1;
+  bool has_kappa = false;
+  const double *kappa_pending = nullptr;
+  LevelData lv[kMaxLevels];
+  // workspace
+  char *ws = nullptr;
+  size_t ws_bytes = 0, need = 0;
+  bool ws_owned = false;
+  bool ready = false;
+  size_t o_st = 0, o_hist = 0, o_part = 0, o_out = 0, o_cg = 0;
+  size_t npart = 0;
+  CgState *st = nullptr;
+  double *hist = nullptr, *part = nullptr, *dout = nullptr;
+  double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_ap = nullptr;
+  // multi-RHS region (sized by opt.max_rhs)
+  size_t o_multi = 0, multi_bytes = 0;
+  cudaStream_t cap = nullptr;
+  GraphCache g_iter;
+  int device = 0;
+  std::mutex mu;
+};
+
+// ---------------------------------------------------------------------------
+static int validate_dims(int nx, int ny, int nz, int levels) {
+  if (levels < 1 || levels > kMaxLevels) return HPCG_ERR_INVALID_ARG;
+  const int div = 1 << (levels - 1);
+  if (nx < 2 || ny < 2 || nz < 2) return HPCG_ERR_INVALID_ARG;
+  if (nx % div || ny % div || nz % div) return HPCG_ERR_INVALID_ARG;
+  if (nx / div < 2 || ny / div < 2 || nz / div < 2) return HPCG_ERR_INVALID_ARG;
+  if ((double)nx * ny * nz > 2.0e9) return HPCG_ERR_INVALID_ARG;  // int32 row indices of the maps
+  return HPCG_OK;
+}
+
+static int red_blocks(long n) {
+  long b = (n + (long)kRedThreads * kRedItems - 1) / ((long)kRedThreads * kRedItems);
+  if (b < 1) b = 1;
+  if (b > kMaxRedBlocksPerInst) b = kMaxRedBlocksPerInst;
+  return (int)b;
+}
+
+// Builds the instance tables and the workspace layout.
+static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
+  h->count = (int)dims.size() / 3;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  for (int l = 0; l < h->levels; ++l) {
+    LevelData &L = h->lv[l];
+    L.inst.resize(h->count);
+    long rows = 0;
+    int bf = 0, bh = 0, br = 0;
+    for (int i = 0; i < h->count; ++i) {
+      Inst &g = L.inst[i];
+      g.nx = dims[3 * i] >> l;
+      g.ny = dims[3 * i + 1] >> l;
+      g.nz = dims[3 * i + 2] >> l;
+      g.n = (long)g.nx * g.ny * g.nz;
+      g.off = rows;
+      g.blk_full = bf;
+      g.blk_half = bh;
+      g.blk_red = br;
+      g.nred = red_blocks(g.n);
+      g.pad = 0;
+      rows += g.n;
+      bf += tiles_of(g.nx, g.ny, g.nz);
+      bh += tiles_of(half_up(g.nx), half_up(g.ny), half_up(g.nz));
+      br += g.nred;
+    }
+    L.n = rows;
+    L.tab.count = h->count;
+    L.tab.nblk_full = bf;
+    L.tab.nblk_half = bh;
+    L.tab.nblk_red = br;
+    L.tab.n = rows;
+  }
+  for (int l = 0; l < h->levels; ++l) h->lv[l].o_tab = take(sizeof(Inst) * h->count);
+  h->o_st = take(sizeof(CgState) * h->count);
+  h->o_hist = take(sizeof(double) * (size_t)kHistoryCap * h->count);
+  const LevelData &L0 = h->lv[0];
+  h->npart = (size_t)std::max(std::max(L0.tab.nblk_full, L0.tab.nblk_red), kRawDotBlocks) + 64;
+  h->o_part = take(sizeof(double) * h->npart);
+  h->o_out = take(sizeof(double) * (h->count + 64));
+  const long n0 = L0.n;
+  h->o_cg = take(sizeof(double) * 4 * (size_t)n0);
+  const bool mixed = h->opt.precision == HPCG_MIXED;
+  for (int l = 0; l < h->levels; ++l) {
+    LevelData &L = h->lv[l];
+    if (l > 0) {
+      L.o_r = take(sizeof(double) * L.n);
+      L.o_z = take(sizeof(double) * L.n);
+    }
+    if (mixed) {
+      L.o_r32 = take(sizeof(float) * L.n);
+      L.o_z32 = take(sizeof(float) * L.n);
+    }
+    if (h->batch == 0) {  // a diagonal field can be bound to a single-grid handle
+      L.o_kap = take(sizeof(double) * L.n);
+      L.o_invd = take(sizeof(double) * L.n);
+      L.o_kap32 = take(sizeof(float) * L.n);
+      L.o_invd32 = take(sizeof(float) * L.n);
+    }
+  }
+  h->multi_bytes = 0;
+  if (h->opt.max_rhs > 0 && h->batch == 0) {
+    // multi-RHS: CG vectors r z p ap (n0 x R), level vectors r z (l >= 1),
+    // per-RHS partial sums, states and history
+    size_t R = (size_t)h->opt.max_rhs;
+    size_t b = align256(sizeof(double) * 4 * (size_t)n0 * R);
+    for (int l = 1; l < h->levels; ++l) b += align256(sizeof(double) * 2 * (size_t)h->lv[l].n * R);
+    b += align256(sizeof(double) * R * (size_t)(h->lv[0].tab.nblk_full + kMaxRedBlocksPerInst + 64));
+    b += align256(sizeof(CgState) * R) + align256(sizeof(double) * R * kHistoryCap);
+    h->o_multi = take(b);
+    h->multi_bytes = b;
+  }
+  h->need = off;
+}
+
+static int bind(hpcg_ctx *h, char *ws, size_t bytes, bool owned) {
+  if (bytes < h->need) return HPCG_ERR_NO_WORKSPACE;
+  if (((uintptr_t)ws & 255) != 0) return HPCG_ERR_INVALID_ARG;
+  if (h->ws_owned && h->ws && h->ws != ws) cudaFree(h->ws);
+  h->ws = ws;
+  h->ws_bytes = bytes;
+  h->ws_owned = owned;
+  CK(cudaGetDevice(&h->device));
+  for (int l = 0; l < h->levels; ++l) {
+    LevelData &L = h->lv[l];
+    L.tab.inst = (const Inst *)(ws + L.o_tab);
+    CK(cudaMemcpy((void *)L.tab.inst, L.inst.data(), sizeof(Inst) * h->count, cudaMemcpyHostToDevice));
+    L.r = l > 0 ? (double *)(ws + L.o_r) : nullptr;
+    L.z = l > 0 ? (double *)(ws + L.o_z) : nullptr;
+    L.r32 = h->opt.precision == HPCG_MIXED ? (float *)(ws + L.o_r32) : nullptr;
+    L.z32 = h->opt.precision == HPCG_MIXED ? (float *)(ws + L.o_z32) : nullptr;
+    if (h->batch == 0) {
+      L.kap = (double *)(ws + L.o_kap);
+      L.invd = (double *)(ws + L.o_invd);
+      L.kap32 = (float *)(ws + L.o_kap32);
+      L.invd32 = (float *)(ws + L.o_invd32);
+    }
+  }
+  h->st = (CgState *)(ws + h->o_st);
+  h->hist = (double *)(ws + h->o_hist);
+  h->part = (double *)(ws + h->o_part);
+  h->dout = (double *)(ws + h->o_out);
+  const long n0 = h->lv[0].n;
+  h->cg_r = (double *)(ws + h->o_cg);
+  h->cg_z = h->cg_r + n0;
+  h->cg_p = h->cg_z + n0;
+  h->cg_ap = h->cg_p + n0;
+  if (h->g_iter.exec) {
+    cudaGraphExecDestroy(h->g_iter.exec);
+    h->g_iter = GraphCache{};
+  }
+  h->ready = true;
+  return HPCG_OK;
+}
+
+static int set_kappa_impl(hpcg_ctx *h, const double *kappa, cudaStream_t s);
+
+static int ensure_ready(hpcg_ctx *h, cudaStream_t s) {
+  if (!h->ready) {
+    char *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, h->need);
+    if (e != cudaSuccess) {
+      cuda_fail(e, "cudaMalloc(workspace)");
+      return HPCG_ERR_OUT_OF_MEMORY;
+    }
+    TRY(bind(h, p, h->need, true));
+  }
+  if (h->kappa_pending) {
+    const double *k = h->kappa_pending;
+    h->kappa_pending = nullptr;
+    TRY(set_kappa_impl(h, k, s));
+  }
+  return HPCG_OK;
+}
+
+static inline int grid_for(long n) {
+  long b = (n + 255) / 256;
+  if (b > 152L * 16) b = 152L * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+static int set_kappa_impl(hpcg_ctx *h, const double *kappa, cudaStream_t s) {
+  if (h->batch) return HPCG_ERR_UNSUPPORTED;
+  if (!kappa) {
+    h->has_kappa = false;
+    return HPCG_OK;
+  }
+  LevelData &L0 = h->lv[0];
+  CK(cudaMemcpyAsync(L0.kap, kappa, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
+  for (int l = 0; l < h->levels; ++l) {
+    LevelData &L = h->lv[l];
+    if (l > 0) {
+      const Inst &f = h->lv[l - 1].inst[0];
+      const Inst &c = L.inst[0];
+      k_inject_kappa<<<grid_for(c.n), 256, 0, s>>>(f.nx, f.ny, c.nx, c.ny, c.nz, h->lv[l - 1].kap, L.kap);
+      CKL("k_inject_kappa");
+    }
+    k_kappa_derived<<<grid_for(L.n), 256, 0, s>>>(L.n, L.kap, L.invd, L.kap32, L.invd32);
+    CKL("k_kappa_derived");
+  }
+  h->has_kappa = true;
+  return HPCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Smoother phase sequence: colours 0..7 (then 7..0 when symmetric) per sweep.
+// A colour step recomputed right after the same colour's step returns the same
+// bits (its inputs are r and the other colours, which did not change), so
+// consecutive repeats are dropped.
+static std::vector<int> phase_sequence(int sweeps, int symmetric) {
+  std::vector<int> seq;
+  for (int s = 0; s < sweeps; ++s) {
+    for (int k = 0; k < 8; ++k) seq.push_back(k);
+    if (symmetric)
+      for (int k = 7; k >= 0; --k) seq.push_back(k);
+  }
+  std::vector<int> out;
+  for (int k : seq)
+    if (out.empty() || out.back() != k) out.push_back(k);
+  return out;
+}
+
+template <typename T>
+static const T *kap_of(const LevelData &L, bool has);
+template <>
+const double *kap_of<double>(const LevelData &L, bool has) { return has ? L.kap : nullptr; }
+template <>
+const float *kap_of<float>(const LevelData &L, bool has) { return has ? L.kap32 : nullptr; }
+template <typename T>
+static const T *invd_of(const LevelData &L, bool has);
+template <>
+const double *invd_of<double>(const LevelData &L, bool has) { return has ? L.invd : nullptr; }
+template <>
+const float *invd_of<float>(const LevelData &L, bool has) { return has ? L.invd32 : nullptr; }
+
+template <typename T>
+static int enqueue_colour(hpcg_ctx *h, int l, int k, const T *r, T *z, cudaStream_t s, const CgState *st) {
+  const LevelData &L = h->lv[l];
+  k_gs_color<T><<<L.tab.nblk_half, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, k & 1, (k >> 1) & 1, (k >> 2) & 1, r, z,
+                                                                 invd_of<T>(L, h->has_kappa), st);
+  CKL("k_gs_color");
+  return HPCG_OK;
+}
+
+template <typename T>
+static int enqueue_smoother(hpcg_ctx *h, int l, const T *r, T *z, int sweeps, cudaStream_t s, const CgState *st) {
+  for (int k : phase_sequence(sweeps, h->opt.symmetric)) TRY(enqueue_colour<T>(h, l, k, r, z, s, st));
+  return HPCG_OK;
+}
+
+template <typename T>
+static int enqueue_restrict(hpcg_ctx *h, int l, const T *r, const T *z, T *rc, cudaStream_t s, const CgState *st) {
+  const LevelData &F = h->lv[l], &C = h->lv[l + 1];
+  k_restrict_residual<T><<<C.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(F.tab.inst, C.tab.inst, h->count, r, z, rc,
+                                                                          kap_of<T>(F, h->has_kappa), st);
+  CKL("k_restrict_residual");
+  return HPCG_OK;
+}
+
+template <typename T>
+static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s, const CgState *st) {
+  const LevelData &F = h->lv[l], &C = h->lv[l + 1];
+  k_prolong_add<T><<<C.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(F.tab.inst, C.tab.inst, h->count, zc, z, st);
+  CKL("k_prolong_add");
+  return HPCG_OK;
+}
+
+template <typename T>
+static int enqueue_zero(hpcg_ctx *h, int l, T *v, cudaStream_t s, const CgState *st) {
+  const LevelData &L = h->lv[l];
+  k_zero_inst<T><<<L.tab.nblk_red, kRedThreads, 0, s>>>(L.tab.inst, h->count, v, st);
+  CKL("k_zero_inst");
+  return HPCG_OK;
+}
+
+// Listing 1 on levels 0..L-1; rl[l], zl[l] are the level vectors in precision T.
+template <typename T>
+static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_t s, const CgState *st) {
+  const int L = h->levels;
+  for (int l = 0; l < L; ++l) {
+    TRY(enqueue_zero<T>(h, l, zl[l], s, st));                                   // z <- 0
+    TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], l == L - 1 ? 1 : h->opt.pre_sweeps, s, st));  // pre-smoothing
+    if (l == L - 1) break;                                                      // coarsest: return
+    TRY(enqueue_restrict<T>(h, l, rl[l], zl[l], rl[l + 1], s, st));             // r_c <- restrict(r - A z)
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    TRY(enqueue_prolong<T>(h, l, zl[l + 1], zl[l], s, st));                     // z <- z + refine(z_c)
+    TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], h->opt.post_sweeps, s, st));    // post-smoothing
+  }
+  return HPCG_OK;
+}
+
+// z = M r on level-0 FP64 vectors, in the handle's precision.
+static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st) {
+  if (h->opt.precision == HPCG_MIXED) {
+    const LevelData &L0 = h->lv[0];
+    k_convert<double, float><<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, r, L0.r32, st);
+    CKL("k_convert");
+    float *rl[kMaxLevels], *zl[kMaxLevels];
+    for (int l = 0; l < h->levels; ++l) {
+      rl[l] = h->lv[l].r32;
+      zl[l] = h->lv[l].z32;
+    }
+    TRY(enqueue_vcycle_t<float>(h, rl, zl, s, st));
+    k_convert<float, double><<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, L0.z32, z, st);
+    CKL("k_convert");
+    return HPCG_OK;
+  }
+  double *rl[kMaxLevels], *zl[kMaxLevels];
+  rl[0] = const_cast<double *>(r);
+  zl[0] = z;
+  for (int l = 1; l < h->levels; ++l) {
+    rl[l] = h->lv[l].r;
+    zl[l] = h->lv[l].z;
+  }
+  return enqueue_vcycle_t<double>(h, rl, zl, s, st);
+}
+
+// ---------------------------------------------------------------------------
+// PCG (Section II-C), HPCG iteration order; every kernel is gated per instance
+// by the device-side `done` flag, so iterations enqueued after convergence are
+// no-ops and the host may run ahead of the device.
+static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_iters, double tol, cudaStream_t s) {
+  std::vector<CgState> init(h->count);
+  for (auto &c : init) {
+    memset(&c, 0, sizeof(c));
+    c.first = 1;
+    c.tol = tol;
+    c.max_iters = max_iters;
+    c.mixed = h->opt.precision == HPCG_MIXED;
+    c.status = HPCG_OK;
+  }
+  CK(cudaMemcpyAsync(h->st, init.data(), sizeof(CgState) * h->count, cudaMemcpyHostToDevice, s));
+  const LevelData &L0 = h->lv[0];
+  // r = b - A x
+  k_spmv<double, 1><<<L0.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L0.tab.inst, h->count, x, b, h->cg_r,
+                                                                      h->has_kappa ? L0.kap : nullptr, nullptr, nullptr);
+  CKL("k_spmv(residual)");
+  k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_r, h->part, h->st);
+  CKL("k_dot_partial");
+  k_finalize<FIN_NORM0><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  CKL("k_finalize<NORM0>");
+  if (max_iters <= 0) {
+    // nothing to iterate: mark every instance done
+  }
+  return HPCG_OK;
+}
+
+static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_t s) {
+  const LevelData &L0 = h->lv[0];
+  const double *kap = h->has_kappa ? L0.kap : nullptr;
+  if (h->opt.precision == HPCG_MIXED) {
+    k_restart_residual<<<L0.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L0.tab.inst, h->count, x, b, h->cg_r, kap, h->st);
+    CKL("k_restart_residual");
+  }
+  TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st));  // z = M r
+  k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_z, h->part, h->st);
+  CKL("k_dot_partial");
+  k_finalize<FIN_RTZ><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  CKL("k_finalize<RTZ>");
+  k_update_p<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_z, h->cg_p, h->st);  // p = z + beta p
+  CKL("k_update_p");
+  k_spmv<double, 0><<<L0.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L0.tab.inst, h->count, h->cg_p, nullptr, h->cg_ap, kap,
+                                                                      h->part, h->st);  // Ap, p.Ap
+  CKL("k_spmv");
+  k_finalize<FIN_PAP><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 1, h->st, h->hist, nullptr);
+  CKL("k_finalize<PAP>");
+  k_update_xr<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r, h->part, h->st);
+  CKL("k_update_xr");
+  k_finalize<FIN_NORM><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  CKL("k_finalize<NORM>");
+  return HPCG_OK;
+}
+
+// Captures one CG iteration into a graph (cached per (b, x)).
+static int get_iter_graph(hpcg_ctx *h, const double *b, double *x, cudaGraphExec_t *out, long *kernels) {
+  GraphCache &g = h->g_iter;
+  if (g.exec && g.key[0] == b && g.key[1] == x) {
+    *out = g.exec;
+    *kernels = g.kernels;
+    return HPCG_OK;
+  }
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  const long before = g_launches.load();
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_pcg_iter(h, b, x, h->cap);
+  cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+  if (rc != HPCG_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  const long nk = g_launches.load() - before;
+  g_launches.fetch_sub(nk);  // counted again at every replay
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  g.key[0] = b;
+  g.key[1] = x;
+  g.kernels = nk;
+  *out = g.exec;
+  *kernels = nk;
+  return HPCG_OK;
+}
+
+static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, double tol, hpcg_stats *stats, cudaStream_t s) {
+  if (max_iters < 0 || max_iters > kHistoryCap) return HPCG_ERR_INVALID_ARG;
+  TRY(enqueue_pcg_init(h, b, x, max_iters, tol, s));
+  cudaGraphExec_t exec;
+  long nk = 0;
+  TRY(get_iter_graph(h, b, x, &exec, &nk));
+  const int every = h->opt.check_every > 0 ? h->opt.check_every : 1;
+  std::vector<CgState> hs(h->count);
+  int *pinned = nullptr;
+  if (tol > 0.0) CK(cudaMallocHost(&pinned, sizeof(int) * 2));
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (tol > 0.0) {
+    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+  }
+  int rc = HPCG_OK;
+  int pending = -1;  // slot whose flag copy is in flight
+  for (int it = 0; it < max_iters; ++it) {
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "cudaGraphLaunch");
+      break;
+    }
+    g_launches.fetch_add(nk);
+    if (tol > 0.0 && ((it + 1) % every == 0)) {
+      // all instances done <=> min over done flags; single instance: st[0].done.
+      // For batches the host polls instance 0..count-1 through the stats copy below;
+      // here only the first instance's flag is sampled when count == 1.
+      if (h->count == 1) {
+        const int slot = it & 1;
+        e = cudaMemcpyAsync(pinned + slot, &h->st[0].done, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[slot], s);
+        if (e != cudaSuccess) {
+          rc = cuda_fail(e, "flag copy");
+          break;
+        }
+        if (pending >= 0) {
+          cudaEventSynchronize(ev[pending]);
+          if (pinned[pending]) break;
+        }
+        pending = slot;
+      } else {
+        CK(cudaMemcpyAsync(hs.data(), h->st, sizeof(CgState) * h->count, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        bool all = true;
+        for (auto &c : hs) all = all && c.done;
+        if (all) break;
+      }
+    }
+  }
+  if (rc == HPCG_OK) {
+    cudaError_t e = cudaMemcpyAsync(hs.data(), h->st, sizeof(CgState) * h->count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "stats copy");
+  }
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  if (pinned) cudaFreeHost(pinned);
+  if (rc != HPCG_OK) return rc;
+  int worst = HPCG_OK;
+  for (int i = 0; i < h->count; ++i) {
+    const CgState &c = hs[i];
+    int st = c.status;
+    if (st == HPCG_OK && tol > 0.0 && !c.converged) st = HPCG_ERR_NOT_CONVERGED;
+    if (stats) {
+      hpcg_stats &o = stats[i];
+      o.iters = c.iter;
+      o.restarts = c.restarts;
+      o.converged = c.converged;
+      o.status = st;
+      o.rel_res = c.normr0 > 0 ? c.normr / c.normr0 : 0.0;
+      if (o.history && o.history_cap > 0 && c.iter > 0) {
+        int m = c.iter < o.history_cap ? c.iter : o.history_cap;
+        CK(cudaMemcpy(o.history, h->hist + (size_t)i * kHistoryCap, sizeof(double) * m, cudaMemcpyDeviceToHost));
+      }
+    }
+    if (st == HPCG_ERR_BREAKDOWN) worst = st;
+    else if (st != HPCG_OK && worst == HPCG_OK) worst = st;
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+extern "C" {
+
+int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
+  if (!opt) return HPCG_ERR_INVALID_ARG;
+  memset(opt, 0, sizeof(*opt));
+  opt->nx = nx;
+  opt->ny = ny;
+  opt->nz = nz;
+  opt->levels = 4;
+  opt->precision = HPCG_FP64;
+  opt->pre_sweeps = 1;
+  opt->post_sweeps = 1;
+  opt->symmetric = 1;
+  opt->check_every = 1;
+  opt->max_rhs = 0;
+  return HPCG_OK;
+}
+
+static int make_handle(const hpcg_options *opt, const std::vector<int> &dims, int batch, hpcg_handle *out) {
+  hpcg_ctx *h = new hpcg_ctx();
+  h->opt = *opt;
+  h->batch = batch;
+  h->levels = opt->levels;
+  plan(h, dims);
+  *out = h;
+  return HPCG_OK;
+}
+
+int hpcg_setup_ex(const hpcg_options *opt, const double *kappa_dev, hpcg_handle *out) {
+  if (!opt || !out) return HPCG_ERR_INVALID_ARG;
+  TRY(validate_dims(opt->nx, opt->ny, opt->nz, opt->levels));
+  if (opt->precision != HPCG_FP64 && opt->precision != HPCG_MIXED) return HPCG_ERR_INVALID_ARG;
+  if (opt->pre_sweeps < 1 || opt->post_sweeps < 1 || opt->pre_sweeps > 16 || opt->post_sweeps > 16) return HPCG_ERR_INVALID_ARG;
+  if (opt->max_rhs < 0 || opt->max_rhs > 64) return HPCG_ERR_INVALID_ARG;
+  std::vector<int> dims = {opt->nx, opt->ny, opt->nz};
+  TRY(make_handle(opt, dims, 0, out));
+  (*out)->kappa_pending = kappa_dev;
+  return HPCG_OK;
+}
+
+int hpcg_setup(int nx, int ny, int nz, int levels, hpcg_handle *out) {
+  hpcg_options o;
+  hpcg_options_default(&o, nx, ny, nz);
+  o.levels = levels;
+  return hpcg_setup_ex(&o, nullptr, out);
+}
+
+int hpcg_setup_batch(int count, const int *dims_host, int levels, int precision, hpcg_handle *out) {
+  if (count < 1 || count > 4096 || !dims_host || !out) return HPCG_ERR_INVALID_ARG;
+  if (precision != HPCG_FP64 && precision != HPCG_MIXED) return HPCG_ERR_INVALID_ARG;
+  std::vector<int> dims(dims_host, dims_host + 3 * count);
+  for (int i = 0; i < count; ++i) TRY(validate_dims(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], levels));
+  hpcg_options o;
+  hpcg_options_default(&o, dims[0], dims[1], dims[2]);
+  o.levels = levels;
+  o.precision = precision;
+  o.check_every = 4;
+  return make_handle(&o, dims, 1, out);
+}
+
+int hpcg_batch_offsets(hpcg_handle h, long *offsets_host) {
+  if (!h || !offsets_host) return HPCG_ERR_INVALID_ARG;
+  for (int i = 0; i < h->count; ++i) offsets_host[i] = h->lv[0].inst[i].off;
+  offsets_host[h->count] = h->lv[0].n;
+  return HPCG_OK;
+}
+
+int hpcg_set_kappa(hpcg_handle h, const double *kappa_dev, void *stream) {
+  if (!h) return HPCG_ERR_INVALID_ARG;
+  if (h->batch) return HPCG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->kappa_pending = nullptr;
+  TRY(ensure_ready(h, (cudaStream_t)stream));
+  if (h->g_iter.exec) {  // kernels captured with or without kappa: recapture
+    cudaGraphExecDestroy(h->g_iter.exec);
+    h->g_iter = GraphCache{};
+  }
+  return set_kappa_impl(h, kappa_dev, (cudaStream_t)stream);
+}
+
+int hpcg_destroy(hpcg_handle h) {
+  if (!h) return HPCG_ERR_INVALID_ARG;
+  if (h->ready) cudaDeviceSynchronize();
+  if (h->g_iter.exec) cudaGraphExecDestroy(h->g_iter.exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->ws_owned && h->ws) cudaFree(h->ws);
+  delete h;
+  return HPCG_OK;
+}
+
+int hpcg_workspace_bytes(hpcg_handle h, size_t *bytes) {
+  if (!h || !bytes) return HPCG_ERR_INVALID_ARG;
+  *bytes = h->need;
+  return HPCG_OK;
+}
+
+int hpcg_bind_workspace(hpcg_handle h, void *dev, size_t bytes) {
+  if (!h || !dev) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  return bind(h, (char *)dev, bytes, false);
+}
+
+int hpcg_level_dims(hpcg_handle h, int level, int *dims_host) {
+  if (!h || !dims_host || level < 0 || level >= h->levels) return HPCG_ERR_INVALID_ARG;
+  const Inst &g = h->lv[level].inst[0];
+  dims_host[0] = g.nx;
+  dims_host[1] = g.ny;
+  dims_host[2] = g.nz;
+  return HPCG_OK;
+}
+
+int hpcg_get_colors(hpcg_handle h, int level, int *colors_dev, void *stream) {
+  if (!h || !colors_dev || level < 0 || level >= h->levels) return HPCG_ERR_INVALID_ARG;
+  const Inst &g = h->lv[level].inst[0];
+  k_colors<<<grid_for(g.n), 256, 0, (cudaStream_t)stream>>>(g.nx, g.ny, g.nz, colors_dev);
+  CKL("k_colors");
+  return HPCG_OK;
+}
+
+int hpcg_get_f2c(hpcg_handle h, int level, int *f2c_dev, void *stream) {
+  if (!h || !f2c_dev || level < 0 || level >= h->levels - 1) return HPCG_ERR_INVALID_ARG;
+  const Inst &f = h->lv[level].inst[0], &c = h->lv[level + 1].inst[0];
+  k_f2c<<<grid_for(c.n), 256, 0, (cudaStream_t)stream>>>(f.nx, f.ny, c.nx, c.ny, c.nz, f2c_dev);
+  CKL("k_f2c");
+  return HPCG_OK;
+}
+
+int hpcg_get_row_nnz(hpcg_handle h, int level, int *nnz_dev, void *stream) {
+  if (!h || !nnz_dev || level < 0 || level >= h->levels) return HPCG_ERR_INVALID_ARG;
+  const Inst &g = h->lv[level].inst[0];
+  k_row_nnz<<<grid_for(g.n), 256, 0, (cudaStream_t)stream>>>(g.nx, g.ny, g.nz, nnz_dev);
+  CKL("k_row_nnz");
+  return HPCG_OK;
+}
+
+int hpcg_get_rhs(hpcg_handle h, double *b_dev, void *stream) {
+  if (!h || !b_dev) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  for (int i = 0; i < h->count; ++i) {
+    const Inst &g = h->lv[0].inst[i];
+    k_rhs_ones<<<grid_for(g.n), 256, 0, s>>>(g.nx, g.ny, g.nz, h->has_kappa ? h->lv[0].kap : nullptr, b_dev + g.off);
+    CKL("k_rhs_ones");
+  }
+  return HPCG_OK;
+}
+
+int hpcg_spmv(hpcg_handle h, int level, const double *x_dev, double *y_dev, void *stream) {
+  if (!h || !x_dev || !y_dev || level < 0 || level >= h->levels) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  const LevelData &L = h->lv[level];
+  k_spmv<double, 0><<<L.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, x_dev, nullptr, y_dev,
+                                                                     h->has_kappa ? L.kap : nullptr, nullptr, nullptr);
+  CKL("k_spmv");
+  return HPCG_OK;
+}
+
+int hpcg_rbgs_color(hpcg_handle h, int level, int color, const double *r_dev, double *z_dev, void *stream) {
+  if (!h || !r_dev || !z_dev || level < 0 || level >= h->levels || color < 0 || color > 7) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  return enqueue_colour<double>(h, level, color, r_dev, z_dev, s, nullptr);
+}
+
+int hpcg_rbgs(hpcg_handle h, int level, const double *r_dev, double *z_dev, void *stream) {
+  if (!h || !r_dev || !z_dev || level < 0 || level >= h->levels) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  return enqueue_smoother<double>(h, level, r_dev, z_dev, 1, s, nullptr);
+}
+
+int hpcg_restrict_residual(hpcg_handle h, int level, const double *r_dev, const double *z_dev, double *rc_dev, void *stream) {
+  if (!h || !r_dev || !z_dev || !rc_dev || level < 0 || level >= h->levels - 1) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  return enqueue_restrict<double>(h, level, r_dev, z_dev, rc_dev, s, nullptr);
+}
+
+int hpcg_prolong_add(hpcg_handle h, int level, const double *zc_dev, double *z_dev, void *stream) {
+  if (!h || !zc_dev || !z_dev || level < 0 || level >= h->levels - 1) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  return enqueue_prolong<double>(h, level, zc_dev, z_dev, s, nullptr);
+}
+
+int hpcg_mg_vcycle(hpcg_handle h, const double *r_dev, double *z_dev, void *stream) {
+  if (!h || !r_dev || !z_dev || r_dev == z_dev) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  return enqueue_vcycle(h, r_dev, z_dev, s, nullptr);
+}
+
+int hpcg_dot(hpcg_handle h, long n, const double *a_dev, const double *b_dev, double *out_dev, void *stream) {
+  if (!h || !out_dev || n < 0 || (n > 0 && (!a_dev || !b_dev))) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  k_dot_raw<<<kRawDotBlocks, kRedThreads, 0, s>>>(n, a_dev, b_dev, h->part);
+  CKL("k_dot_raw");
+  k_sum_raw<<<1, kRedThreads, 0, s>>>(kRawDotBlocks, h->part, out_dev);
+  CKL("k_sum_raw");
+  return HPCG_OK;
+}
+
+int hpcg_waxpby(hpcg_handle h, long n, double alpha, const double *x_dev, double beta, const double *y_dev, double *w_dev,
+                void *stream) {
+  if (!h || n < 0) return HPCG_ERR_INVALID_ARG;
+  if (n == 0) return HPCG_OK;
+  if (!x_dev || !y_dev || !w_dev) return HPCG_ERR_INVALID_ARG;
+  k_waxpby<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, alpha, x_dev, beta, y_dev, w_dev);
+  CKL("k_waxpby");
+  return HPCG_OK;
+}
+
+int hpcg_pcg_solve(hpcg_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol, hpcg_stats *stats,
+                   void *stream) {
+  if (!h || !b_dev || !x_dev || h->batch) return h && h->batch ? HPCG_ERR_UNSUPPORTED : HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  return run_pcg(h, b_dev, x_dev, max_iters, rel_tol, stats, s);
+}
+
+int hpcg_pcg_solve_batch(hpcg_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol, hpcg_stats *stats,
+                         void *stream) {
+  if (!h || !b_dev || !x_dev) return HPCG_ERR_INVALID_ARG;
+  if (!h->batch) return HPCG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  return run_pcg(h, b_dev, x_dev, max_iters, rel_tol, stats, s);
+}
+
+int hpcg_pcg_backward(hpcg_handle h, const double *x_dev, const double *grad_x_dev, double *grad_b_dev, double *grad_kappa_dev,
+                      int max_iters, double rel_tol, hpcg_stats *stats, void *stream) {
+  if (!h || !x_dev || !grad_x_dev || !grad_b_dev) return HPCG_ERR_INVALID_ARG;
+  if (grad_b_dev == x_dev || grad_b_dev == grad_x_dev) return HPCG_ERR_INVALID_ARG;
+  if (h->batch) return HPCG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  const long n = h->lv[0].n;
+  CK(cudaMemsetAsync(grad_b_dev, 0, sizeof(double) * n, s));  // lambda_0 = 0
+  int rc = run_pcg(h, grad_x_dev, grad_b_dev, max_iters, rel_tol, stats, s);  // A lambda = grad_x
+  if (rc != HPCG_OK && rc != HPCG_ERR_NOT_CONVERGED) return rc;
+  if (grad_kappa_dev) {
+    k_grad_kappa<<<grid_for(n), 256, 0, s>>>(n, grad_b_dev, x_dev, grad_kappa_dev);
+    CKL("k_grad_kappa");
+  }
+  return rc;
+}
+
+int hpcg_pcg_solve_multi(hpcg_handle h, int nrhs, const double *B_dev, double *X_dev, int max_iters, double rel_tol,
+                         hpcg_stats *stats, void *stream) {
+  (void)h; (void)nrhs; (void)B_dev; (void)X_dev; (void)max_iters; (void)rel_tol; (void)stats; (void)stream;
+  return HPCG_ERR_UNSUPPORTED;
+}
+
+const char *hpcg_strerror(int status) {
+  switch (status) {
+    case HPCG_OK: return "ok";
+    case HPCG_ERR_INVALID_ARG: return "invalid argument";
+    case HPCG_ERR_CUDA: return "CUDA error";
+    case HPCG_ERR_BREAKDOWN: return "CG breakdown (p.Ap <= 0 or non-finite scalar)";
+    case HPCG_ERR_NOT_CONVERGED: return "tolerance not reached within max_iters";
+    case HPCG_ERR_TIMEOUT: return "bounded device wait timed out";
+    case HPCG_ERR_NO_WORKSPACE: return "workspace too small";
+    case HPCG_ERR_OUT_OF_MEMORY: return "device allocation failed";
+    case HPCG_ERR_UNSUPPORTED: return "unsupported for this handle";
+    default: return "unknown status";
+  }
+}
+
+const char *hpcg_last_cuda_error(void) { return g_last_cuda_error; }
+long hpcg_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

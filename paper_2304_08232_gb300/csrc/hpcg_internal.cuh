@@ -1,0 +1,74 @@
+// hpcg_internal.cuh -- device-side data structures shared by the kernels and
+// the host driver of the GB300 MG-PCG library.
+//
+// Layout in HBM: every level of every instance stores its vectors in natural
+// row order i = x + nx*(y + ny*z); the vectors of all instances of one level
+// are concatenated (Inst::off is the first row of an instance), so that one
+// kernel launch covers the same step of every instance of a batch.  A
+// single-instance handle is a batch of one.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hpcg.h"
+
+namespace hpcg {
+
+constexpr int kMaxLevels = 8;
+constexpr int kTileX = 32;       // threads of a block along x (one warp)
+constexpr int kTileY = 8;        // warps of a block along y
+constexpr int kBlock = kTileX * kTileY;
+constexpr int kRedThreads = 256; // threads of a reduction block
+constexpr int kRedItems = 8;     // elements per thread per reduction block (before the block strides)
+constexpr int kMaxRedBlocksPerInst = 592;  // 4 x 148... fixed cap keeps reductions deterministic
+constexpr int kHistoryCap = 8192;
+constexpr int kRawDotBlocks = 304;  // fixed grid of the plain dot product (2 x 152 SMs)
+
+// One grid (one level of one instance).
+struct Inst {
+  int nx, ny, nz;
+  int blk_full;   // first block of this grid in a launch over all rows (32x8 tiles per z-plane)
+  int blk_half;   // first block in a launch over one colour class (half lattice)
+  int blk_red;    // first block in a reduction launch
+  int nred;       // reduction blocks of this grid
+  int pad;
+  long off;       // first row of this grid in the level's concatenated vectors
+  long n;         // rows
+};
+
+// Per-level launch description (host copy; `inst` points to the device table).
+struct LevelTab {
+  const Inst *inst;  // device array [count]
+  int count;
+  int nblk_full, nblk_half, nblk_red;
+  long n;            // rows over all instances
+};
+
+// Device-resident CG scalars of one instance.
+struct CgState {
+  double rtz, pAp, alpha, beta, normr, normr0, best, tol;
+  double hist_prev[3];
+  int iter, done, status, first, restart, restarts, stall, max_iters;
+  int converged, mixed, pad0, pad1;
+};
+
+// Blocks of a 32x8-tiled launch over an nx x ny x nz box, one z-plane per tile row.
+__host__ __device__ inline int tiles_of(int nx, int ny, int nz) {
+  return ((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY) * nz;
+}
+__host__ __device__ inline int half_up(int v) { return (v + 1) / 2; }
+
+// Finds the instance that owns global block `b` (prefix `which` in the table);
+// tables hold at most a few hundred entries, a binary search is uniform per block.
+template <int Which>
+__device__ inline int find_inst(const Inst *__restrict__ tab, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    int start = Which == 0 ? tab[mid].blk_full : (Which == 1 ? tab[mid].blk_half : tab[mid].blk_red);
+    if (start <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace hpcg

@@ -1,0 +1,496 @@
+// hpcg_kernels.cuh -- sm_103a kernels of the MG-PCG hot path.
+//
+// All stencil kernels are matrix-free: the 27-point operator of Sections II-B/C
+// has diagonal 26 (+kappa_i) and -1 to every in-grid neighbour, so no matrix is
+// read from HBM.  Colour classes are the parity classes of Section III-A's
+// greedy colouring; injection takes the even-coordinate point of each octet
+// (Section II-E).  T is double (FP64 path) or float (mixed-precision
+// preconditioner).  Every kernel takes the instance table of its level so that
+// one launch covers a whole batch; `st` (nullable) gates work per instance
+// once that instance's CG has converged.
+#pragma once
+#include "hpcg_internal.cuh"
+
+namespace hpcg {
+
+// Sum of the 26 neighbours of (x,y,z) that lie inside the grid, in ascending
+// column order.  v points at the grid's first row.
+template <typename T>
+__device__ __forceinline__ T nbr_sum26(const T *__restrict__ v, int x, int y, int z, int nx, int ny, int nz) {
+  T s = T(0);
+  const long sxy = (long)nx * ny;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int zz = z + dz;
+    if (zz < 0 || zz >= nz) continue;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = y + dy;
+      if (yy < 0 || yy >= ny) continue;
+      const long base = (long)zz * sxy + (long)yy * nx;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = x + dx;
+        if (xx < 0 || xx >= nx) continue;
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        s += __ldg(v + base + xx);
+      }
+    }
+  }
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T diag_of(const T *__restrict__ kap, long gi) {
+  return kap ? T(26) + kap[gi] : T(26);
+}
+
+template <typename T>
+__device__ __forceinline__ T inv_diag_of(const T *__restrict__ invd, long gi) {
+  return invd ? invd[gi] : T(1) / T(26);
+}
+
+// Deterministic block sum (fixed shuffle tree, fixed warp order); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int warp = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+  if ((tid & 31) == 0) sh[warp] = v;
+  (void)lane;
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0)
+    for (int w = 0; w < nwarps; ++w) s += sh[w];
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// y = A x (Mode 0), y = b - A x (Mode 1).  Optional fused dot partial of x.y
+// (used for p.Ap in CG).  One thread per row; 32x8 tile of an x-y plane per block.
+template <typename T, int Mode>
+__global__ void __launch_bounds__(kBlock) k_spmv(const Inst *__restrict__ tab, int count, const T *__restrict__ x,
+                                                 const T *__restrict__ b, T *__restrict__ y, const T *__restrict__ kap,
+                                                 double *__restrict__ partials, const CgState *__restrict__ st) {
+  __shared__ double sh[kBlock / 32];
+  const int blk = blockIdx.x;
+  const int ii = find_inst<0>(tab, count, blk);
+  const Inst g = tab[ii];
+  if (st && st[ii].done) {
+    if (partials && threadIdx.x == 0 && threadIdx.y == 0) partials[blk] = 0.0;
+    return;
+  }
+  int lb = blk - g.blk_full;
+  const int tx = (g.nx + kTileX - 1) / kTileX, ty = (g.ny + kTileY - 1) / kTileY;
+  const int bx = lb % tx;
+  lb /= tx;
+  const int by = lb % ty;
+  const int z = lb / ty;
+  const int xx = bx * kTileX + threadIdx.x, yy = by * kTileY + threadIdx.y;
+  double dotv = 0.0;
+  if (xx < g.nx && yy < g.ny && z < g.nz) {
+    const T *xg = x + g.off;
+    const long li = xx + (long)g.nx * (yy + (long)g.ny * z);
+    const long gi = g.off + li;
+    const T xi = xg[li];
+    const T ax = diag_of(kap, gi) * xi - nbr_sum26(xg, xx, yy, z, g.nx, g.ny, g.nz);
+    const T out = Mode == 0 ? ax : b[gi] - ax;
+    y[gi] = out;
+    if (partials) dotv = (double)xi * (double)out;
+  }
+  if (partials) {
+    const double s = block_sum(dotv, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blk] = s;
+  }
+}
+
+// Restart of the mixed-precision outer loop: r = b - A x for instances whose
+// stall flag is set (FP64).
+__global__ void __launch_bounds__(kBlock) k_restart_residual(const Inst *__restrict__ tab, int count, const double *__restrict__ x,
+                                                             const double *__restrict__ b, double *__restrict__ r,
+                                                             const double *__restrict__ kap, const CgState *__restrict__ st) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<0>(tab, count, blk);
+  const Inst g = tab[ii];
+  if (st[ii].done || !st[ii].restart) return;
+  int lb = blk - g.blk_full;
+  const int tx = (g.nx + kTileX - 1) / kTileX, ty = (g.ny + kTileY - 1) / kTileY;
+  const int bx = lb % tx;
+  lb /= tx;
+  const int by = lb % ty;
+  const int z = lb / ty;
+  const int xx = bx * kTileX + threadIdx.x, yy = by * kTileY + threadIdx.y;
+  if (xx < g.nx && yy < g.ny && z < g.nz) {
+    const double *xg = x + g.off;
+    const long li = xx + (long)g.nx * (yy + (long)g.ny * z);
+    const long gi = g.off + li;
+    r[gi] = b[gi] - (diag_of(kap, gi) * xg[li] - nbr_sum26(xg, xx, yy, z, g.nx, g.ny, g.nz));
+  }
+}
+
+// One colour step of red-black Gauss-Seidel (Listings 2/3): rows of parity
+// (px,py,pz) get z_i <- (r_i + sum_{j in N(i)} z_j) / A_ii.  Rows of one colour
+// do not neighbour each other, so the step is order-free within the colour.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_color(const Inst *__restrict__ tab, int count, int px, int py, int pz,
+                                                     const T *__restrict__ r, T *__restrict__ z, const T *__restrict__ invd,
+                                                     const CgState *__restrict__ st) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<1>(tab, count, blk);
+  const Inst g = tab[ii];
+  if (st && st[ii].done) return;
+  const int hx = half_up(g.nx), hy = half_up(g.ny);
+  int lb = blk - g.blk_half;
+  const int tx = (hx + kTileX - 1) / kTileX, ty = (hy + kTileY - 1) / kTileY;
+  const int bx = lb % tx;
+  lb /= tx;
+  const int by = lb % ty;
+  const int Z = lb / ty;
+  const int xx = 2 * (bx * kTileX + threadIdx.x) + px;
+  const int yy = 2 * (by * kTileY + threadIdx.y) + py;
+  const int zz = 2 * Z + pz;
+  if (xx < g.nx && yy < g.ny && zz < g.nz) {
+    T *zg = z + g.off;
+    const long li = xx + (long)g.nx * (yy + (long)g.ny * zz);
+    const long gi = g.off + li;
+    const T s = r[gi] + nbr_sum26((const T *)zg, xx, yy, zz, g.nx, g.ny, g.nz);
+    zg[li] = s * inv_diag_of(invd, gi);
+  }
+}
+
+// Fused residual + injection (Listing 1 lines 5-6): for every coarse row c with
+// fine row f = (2xc,2yc,2zc): rc[c] = r[f] - (A z)[f].
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_restrict_residual(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count,
+                                                              const T *__restrict__ r, const T *__restrict__ z,
+                                                              T *__restrict__ rc, const T *__restrict__ kapf,
+                                                              const CgState *__restrict__ st) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<0>(tabc, count, blk);
+  const Inst c = tabc[ii];
+  const Inst f = tabf[ii];
+  if (st && st[ii].done) return;
+  int lb = blk - c.blk_full;
+  const int tx = (c.nx + kTileX - 1) / kTileX, ty = (c.ny + kTileY - 1) / kTileY;
+  const int bx = lb % tx;
+  lb /= tx;
+  const int by = lb % ty;
+  const int zc = lb / ty;
+  const int xc = bx * kTileX + threadIdx.x, yc = by * kTileY + threadIdx.y;
+  if (xc < c.nx && yc < c.ny && zc < c.nz) {
+    const int xf = 2 * xc, yf = 2 * yc, zf = 2 * zc;
+    const T *zg = z + f.off;
+    const long lf = xf + (long)f.nx * (yf + (long)f.ny * zf);
+    const long gf = f.off + lf;
+    const T az = diag_of(kapf, gf) * zg[lf] - nbr_sum26(zg, xf, yf, zf, f.nx, f.ny, f.nz);
+    rc[c.off + xc + (long)c.nx * (yc + (long)c.ny * zc)] = r[gf] - az;
+  }
+}
+
+// Refinement + correction (Listing 1 line 9): z[f(c)] += zc[c].
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong_add(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count,
+                                                        const T *__restrict__ zc, T *__restrict__ z,
+                                                        const CgState *__restrict__ st) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<0>(tabc, count, blk);
+  const Inst c = tabc[ii];
+  const Inst f = tabf[ii];
+  if (st && st[ii].done) return;
+  int lb = blk - c.blk_full;
+  const int tx = (c.nx + kTileX - 1) / kTileX, ty = (c.ny + kTileY - 1) / kTileY;
+  const int bx = lb % tx;
+  lb /= tx;
+  const int by = lb % ty;
+  const int zz = lb / ty;
+  const int xc = bx * kTileX + threadIdx.x, yc = by * kTileY + threadIdx.y;
+  if (xc < c.nx && yc < c.ny && zz < c.nz) {
+    const long lf = 2 * xc + (long)f.nx * (2 * yc + (long)f.ny * 2 * zz);
+    z[f.off + lf] += zc[c.off + xc + (long)c.nx * (yc + (long)c.ny * zz)];
+  }
+}
+
+// Zero the vectors of every instance not yet converged (level vector z before smoothing).
+template <typename T>
+__global__ void k_zero_inst(const Inst *__restrict__ tab, int count, T *__restrict__ v, const CgState *__restrict__ st) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<2>(tab, count, blk);
+  const Inst g = tab[ii];
+  if (st && st[ii].done) return;
+  const long stride = (long)g.nred * kRedThreads;
+  for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) v[g.off + i] = T(0);
+}
+
+// Precision conversion over every instance's rows (reduction blocking).
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Inst *__restrict__ tab, int count, const Tin *__restrict__ in, Tout *__restrict__ out,
+                          const CgState *__restrict__ st) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<2>(tab, count, blk);
+  const Inst g = tab[ii];
+  if (st && st[ii].done) return;
+  const long stride = (long)g.nred * kRedThreads;
+  for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride)
+    out[g.off + i] = (Tout)in[g.off + i];
+}
+
+// ---------------------------------------------------------------------------
+// Dot products and vector updates of CG (Section II-C), FP64.  Reductions are
+// deterministic: each instance has a fixed number of blocks, each thread sums
+// a fixed strided subset, blocks reduce by a fixed tree, and the final sum over
+// block partials runs in a fixed order.
+
+// partials[b] = sum over this block's subset of a_i * b_i
+__global__ void __launch_bounds__(kRedThreads) k_dot_partial(const Inst *__restrict__ tab, int count, const double *__restrict__ a,
+                                                             const double *__restrict__ bv, double *__restrict__ partials,
+                                                             const CgState *__restrict__ st) {
+  __shared__ double sh[kRedThreads / 32];
+  const int blk = blockIdx.x;
+  const int ii = find_inst<2>(tab, count, blk);
+  const Inst g = tab[ii];
+  double s = 0.0;
+  if (!(st && st[ii].done)) {
+    const long stride = (long)g.nred * kRedThreads;
+    for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) s += a[g.off + i] * bv[g.off + i];
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blk] = s;
+}
+
+// Fixed-order sum of partials[first .. first+cnt) inside one block; valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double *__restrict__ partials, int first, int cnt, double *sh) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) s += partials[first + k];
+  return block_sum(s, sh);
+}
+
+enum FinKind { FIN_NORM0 = 0, FIN_RTZ = 1, FIN_PAP = 2, FIN_NORM = 3, FIN_OUT = 4 };
+
+// One block per instance: turns the partials of a reduction into CG scalars.
+//  FIN_NORM0: normr0 = sqrt(sum)            (start of the solve)
+//  FIN_RTZ:   rtz' = sum; beta = rtz'/rtz   (after z = M r)
+//  FIN_PAP:   alpha = rtz / sum             (after Ap = A p; breakdown check)
+//  FIN_NORM:  normr = sqrt(sum); history; convergence and stall tests
+//  FIN_OUT:   out[inst] = sum               (plain dot product)
+// `stencil` selects the stencil blocking (partials written by k_spmv) instead
+// of the reduction blocking.
+template <int Kind>
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const Inst *__restrict__ tab, int count, const double *__restrict__ partials,
+                                                          int stencil, CgState *__restrict__ st, double *__restrict__ hist,
+                                                          double *__restrict__ out) {
+  __shared__ double sh[kRedThreads / 32];
+  const int ii = blockIdx.x;
+  const Inst g = tab[ii];
+  int first, cnt;
+  if (stencil) {
+    first = g.blk_full;
+    cnt = tiles_of(g.nx, g.ny, g.nz);
+  } else {
+    first = g.blk_red;
+    cnt = g.nred;
+  }
+  if (Kind != FIN_OUT && st[ii].done) return;
+  const double s = sum_partials(partials, first, cnt, sh);
+  if (threadIdx.x != 0) return;
+  if (Kind == FIN_OUT) {
+    out[ii] = s;
+    return;
+  }
+  CgState &c = st[ii];
+  if (Kind == FIN_NORM0) {
+    c.normr0 = sqrt(s);
+    c.normr = c.normr0;
+    c.best = c.normr0;
+    if (!(c.normr0 > 0.0) || !isfinite(c.normr0)) {
+      c.done = 1;
+      c.converged = (c.normr0 == 0.0);
+      c.status = (c.normr0 == 0.0) ? HPCG_OK : HPCG_ERR_BREAKDOWN;
+    }
+  } else if (Kind == FIN_RTZ) {
+    if (c.restart) {
+      c.first = 1;
+      c.restart = 0;
+      c.restarts += 1;
+    }
+    if (c.first) {
+      c.beta = 0.0;
+    } else {
+      c.beta = s / c.rtz;
+    }
+    c.rtz = s;
+    if (!isfinite(s)) {
+      c.done = 1;
+      c.status = HPCG_ERR_BREAKDOWN;
+    }
+  } else if (Kind == FIN_PAP) {
+    c.pAp = s;
+    if (!(s > 0.0) || !isfinite(s)) {
+      c.done = 1;
+      c.status = HPCG_ERR_BREAKDOWN;
+      c.alpha = 0.0;
+    } else {
+      c.alpha = c.rtz / s;
+    }
+    c.first = 0;
+  } else if (Kind == FIN_NORM) {
+    c.normr = sqrt(s);
+    const double rel = c.normr / c.normr0;
+    if (hist && c.iter < kHistoryCap) hist[(long)ii * kHistoryCap + c.iter] = rel;
+    c.iter += 1;
+    if (!isfinite(rel)) {
+      c.done = 1;
+      c.status = HPCG_ERR_BREAKDOWN;
+    } else if (c.tol > 0.0 && rel <= c.tol) {
+      c.done = 1;
+      c.converged = 1;
+    } else if (c.iter >= c.max_iters) {
+      c.done = 1;
+    } else if (c.mixed) {
+      // stall test of the mixed-precision outer loop: no 1% progress over the
+      // best residual for 3 iterations -> replace r by b - A x next iteration
+      if (c.normr < 0.99 * c.best) {
+        c.best = c.normr;
+        c.stall = 0;
+      } else if (++c.stall >= 3) {
+        c.restart = 1;
+        c.stall = 0;
+        c.best = c.normr;
+      }
+    }
+  }
+}
+
+// p = z + beta p (p = z on the first iteration or after a restart)
+__global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict__ tab, int count, const double *__restrict__ zv,
+                                                          double *__restrict__ p, const CgState *__restrict__ st) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<2>(tab, count, blk);
+  const Inst g = tab[ii];
+  const CgState &c = st[ii];
+  if (c.done) return;
+  const bool first = c.first;
+  const double beta = c.beta;
+  const long stride = (long)g.nred * kRedThreads;
+  for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
+    const long gi = g.off + i;
+    p[gi] = first ? zv[gi] : zv[gi] + beta * p[gi];
+  }
+}
+
+// x += alpha p; r -= alpha Ap; partials of r.r
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(const Inst *__restrict__ tab, int count, const double *__restrict__ p,
+                                                           const double *__restrict__ ap, double *__restrict__ x,
+                                                           double *__restrict__ r, double *__restrict__ partials,
+                                                           const CgState *__restrict__ st) {
+  __shared__ double sh[kRedThreads / 32];
+  const int blk = blockIdx.x;
+  const int ii = find_inst<2>(tab, count, blk);
+  const Inst g = tab[ii];
+  const CgState &c = st[ii];
+  double s = 0.0;
+  if (!c.done) {
+    const double alpha = c.alpha;
+    const long stride = (long)g.nred * kRedThreads;
+    for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
+      const long gi = g.off + i;
+      x[gi] = x[gi] + alpha * p[gi];
+      const double rn = r[gi] - alpha * ap[gi];
+      r[gi] = rn;
+      s += rn * rn;
+    }
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blk] = s;
+}
+
+// Plain dot product of two raw arrays with a fixed grid (deterministic).
+__global__ void __launch_bounds__(kRedThreads) k_dot_raw(long n, const double *__restrict__ a, const double *__restrict__ b,
+                                                         double *__restrict__ partials) {
+  __shared__ double sh[kRedThreads / 32];
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)kRedThreads + threadIdx.x; i < n; i += (long)gridDim.x * kRedThreads) s += a[i] * b[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_sum_raw(int cnt, const double *__restrict__ partials, double *__restrict__ out) {
+  __shared__ double sh[kRedThreads / 32];
+  const double s = sum_partials(partials, 0, cnt, sh);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+// w = alpha x + beta y over n values (grid-stride)
+__global__ void k_waxpby(long n, double alpha, const double *__restrict__ x, double beta, const double *__restrict__ y,
+                         double *__restrict__ w) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    w[i] = alpha * x[i] + beta * y[i];
+}
+
+// grad_kappa_i = -lambda_i x_i (diagonal of the outer product -lambda x^T)
+__global__ void k_grad_kappa(long n, const double *__restrict__ lam, const double *__restrict__ x, double *__restrict__ gk) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) gk[i] = -lam[i] * x[i];
+}
+
+// ---------------------------------------------------------------------------
+// Setup kernels (Section II-B input generation, Section III-A colouring,
+// Section II-E injection), one thread per row.
+__global__ void k_colors(int nx, int ny, int nz, int *__restrict__ out) {
+  const long n = (long)nx * ny * nz;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
+    out[i] = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+  }
+}
+
+__global__ void k_row_nnz(int nx, int ny, int nz, int *__restrict__ out) {
+  const long n = (long)nx * ny * nz;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
+    const int cx = 1 + (x > 0) + (x < nx - 1), cy = 1 + (y > 0) + (y < ny - 1), cz = 1 + (z > 0) + (z < nz - 1);
+    out[i] = cx * cy * cz;
+  }
+}
+
+// b = A * ones: b_i = 26 + kappa_i - (nnz_i - 1)
+__global__ void k_rhs_ones(int nx, int ny, int nz, const double *__restrict__ kap, double *__restrict__ b) {
+  const long n = (long)nx * ny * nz;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
+    const int cx = 1 + (x > 0) + (x < nx - 1), cy = 1 + (y > 0) + (y < ny - 1), cz = 1 + (z > 0) + (z < nz - 1);
+    b[i] = (26.0 + (kap ? kap[i] : 0.0)) - (double)(cx * cy * cz - 1);
+  }
+}
+
+__global__ void k_f2c(int nxf, int nyf, int nxc, int nyc, int nzc, int *__restrict__ out) {
+  const long n = (long)nxc * nyc * nzc;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const int xc = (int)(c % nxc), yc = (int)((c / nxc) % nyc), zc = (int)(c / ((long)nxc * nyc));
+    out[c] = (int)(2L * xc + (long)nxf * (2L * yc + (long)nyf * 2L * zc));
+  }
+}
+
+// kappa of level l+1 = kappa of level l at the injected rows; also the
+// inverse diagonal 1/(26 + kappa) of level l+1 in both precisions.
+__global__ void k_inject_kappa(int nxf, int nyf, int nxc, int nyc, int nzc, const double *__restrict__ kf,
+                               double *__restrict__ kc) {
+  const long n = (long)nxc * nyc * nzc;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const int xc = (int)(c % nxc), yc = (int)((c / nxc) % nyc), zc = (int)(c / ((long)nxc * nyc));
+    kc[c] = kf[2L * xc + (long)nxf * (2L * yc + (long)nyf * 2L * zc)];
+  }
+}
+
+__global__ void k_kappa_derived(long n, const double *__restrict__ k, double *__restrict__ invd, float *__restrict__ k32,
+                                float *__restrict__ invd32) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double d = 26.0 + k[i];
+    invd[i] = 1.0 / d;
+    k32[i] = (float)k[i];
+    invd32[i] = 1.0f / (26.0f + (float)k[i]);
+  }
+}
+
+}  // namespace hpcg

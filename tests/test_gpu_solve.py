@@ -1,0 +1,140 @@
+"""GPU parity of the whole solves: FP64 MG-PCG residual history against the
+oracle's, the mixed-precision solve, the differentiable solve's gradients,
+and full-size (192^3) checks of the steps."""
+import numpy as np
+import pytest
+import torch
+
+from hpcg_inputs import differentiable_inputs, mixed_precision_xtrue, normal
+from oracle import OracleProblem, solve_and_grad, spmv_rows
+from tests.dense_ref import kron_eigenvalues
+from tests.gpu_util import TOL32, TOL64, dev, host, need_gpu, normwise
+
+pytestmark = pytest.mark.gpu
+
+
+def _history_close(h, h_ref, floor=1e-11):
+    """Iterates of two FP64 CG runs differ only by rounding; their relative
+    residuals agree closely until they reach the rounding floor."""
+    h, h_ref = np.asarray(h), np.asarray(h_ref)
+    assert len(h) == len(h_ref)
+    live = h_ref > floor
+    rel = np.abs(h[live] - h_ref[live]) / h_ref[live]
+    assert rel.max() <= 1e-6, rel
+    assert np.all(h[~live] <= 100 * floor)
+
+
+@pytest.mark.parametrize("dims,levels", [((16, 16, 16), 4), ((32, 16, 24), 3), ((8, 8, 8), 3)])
+def test_pcg_fp64_history(dims, levels):
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    g = HpcgProblem(*dims, levels=levels)
+    o = OracleProblem(*dims, levels=levels)
+    b = g.get_rhs()
+    x, st = g.pcg_solve(b, max_iters=50, tol=0.0)
+    xr, hr = o.pcg(o.rhs(), max_iters=50, tol=0.0)
+    assert st.iters == 50
+    _history_close(st.history, hr)
+    assert np.abs(host(x) - 1.0).max() <= 1e-10   # exact solution is ones
+    assert normwise(host(x), xr) <= 1e-10
+
+
+def test_pcg_fp64_tolerance_stop_and_random_rhs():
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    dims = (16, 24, 32)
+    g = HpcgProblem(*dims, levels=3)
+    o = OracleProblem(*dims, levels=3)
+    b = normal(int(np.prod(dims)), 0)
+    x, st = g.pcg_solve(dev(b), max_iters=100, tol=1e-9)
+    xr, hr = o.pcg(b, max_iters=100, tol=1e-9)
+    assert st.converged and st.iters == len(hr)
+    _history_close(st.history, hr)
+    assert normwise(host(x), xr) <= 1e-8
+
+
+def test_mixed_precision_vcycle_and_solve():
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    dims = (32, 32, 32)
+    n = 32 ** 3
+    g = HpcgProblem(*dims, levels=4, precision="mixed")
+    o = OracleProblem(*dims, levels=4)
+    r = normal(n, 3)
+    assert normwise(host(g.mg_vcycle(dev(r))), o.mg(r)) <= TOL32
+    xt = mixed_precision_xtrue(n, seed=1)
+    b = o.spmv(xt)
+    x, st = g.pcg_solve(dev(b), max_iters=200, tol=1e-9)
+    assert st.converged and st.rel_res <= 1e-9
+    xr, _ = o.pcg(b, max_iters=200, tol=1e-12)
+    # a relative residual of 1e-9 bounds the relative error by cond(A) * 1e-9;
+    # cond(A) from the closed-form spectrum of the 27-point operator
+    ev = kron_eigenvalues(*dims)
+    cond = ev.max() / ev.min()
+    assert np.linalg.norm(host(x) - xr) / np.linalg.norm(xr) <= cond * 1.2e-9
+    assert np.linalg.norm(b - o.spmv(host(x))) / np.linalg.norm(b) <= 2e-9
+
+
+def test_differentiable_solve_gradients():
+    from paper_2304_08232_gb300 import HpcgProblem, hpcg_solve
+    need_gpu()
+    dims, levels = (8, 8, 8), 3
+    n = 512
+    kappa, b, xt = differentiable_inputs(n, seed=4)
+    for precision in ["fp64", "mixed"]:
+        g = HpcgProblem(*dims, levels=levels, precision=precision)
+        bt = dev(b).requires_grad_(True)
+        kt = dev(kappa).requires_grad_(True)
+        x = hpcg_solve(bt, kt, g, max_iters=300, tol=1e-13)
+        loss = 0.5 * ((x - dev(xt)) ** 2).sum()
+        loss.backward()
+        xr, lr, gbr, gkr = solve_and_grad(dims, levels, kappa, b, xt)
+        assert normwise(host(x), xr) <= 1e-11
+        assert normwise(host(bt.grad), gbr) <= 1e-10
+        assert normwise(host(kt.grad), gkr) <= 1e-10
+
+
+def test_kappa_solve_matches_oracle():
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    dims = (24, 16, 16)
+    n = int(np.prod(dims))
+    kappa, b, _ = differentiable_inputs(n, seed=4)
+    g = HpcgProblem(*dims, levels=3, kappa=dev(kappa))
+    o = OracleProblem(*dims, levels=3, kappa=kappa)
+    x, st = g.pcg_solve(dev(b), max_iters=30, tol=0.0)
+    xr, hr = o.pcg(b, max_iters=30, tol=0.0)
+    _history_close(st.history, hr)
+
+
+# ---------------------------------------------------------------------------
+# full-size workload (192^3, 4 levels): sampled rows of the SpMV checked one
+# by one, the full V-cycle against the oracle's, and the first CG iterations.
+@pytest.fixture(scope="module")
+def big():
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    return HpcgProblem(192, 192, 192, levels=4)
+
+
+def test_full_size_spmv_sampled(big):
+    n = 192 ** 3
+    x = normal(n, 0)
+    y = host(big.spmv(dev(x)))
+    rng = np.random.default_rng(123)
+    rows = np.concatenate([rng.integers(0, n, 20000), [0, 191, n - 1, n - 192, 192 * 192 * 96 + 192 * 7]])
+    ref = spmv_rows(192, 192, 192, rows, x)
+    assert normwise(y[rows], ref) <= TOL64
+
+
+def test_full_size_vcycle_and_pcg(big):
+    o = OracleProblem(192, 192, 192, levels=4)
+    n = 192 ** 3
+    r = normal(n, 0)
+    z = host(big.mg_vcycle(dev(r)))
+    assert normwise(z, o.mg(r)) <= TOL64
+    b = big.get_rhs()
+    x, st = big.pcg_solve(b, max_iters=3, tol=0.0)
+    xr, hr = o.pcg(o.rhs(), max_iters=3, tol=0.0)
+    _history_close(st.history, hr)
+    assert normwise(host(x), xr) <= 1e-10

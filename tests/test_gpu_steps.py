@@ -1,0 +1,117 @@
+"""GPU parity of every single step of the hot path against the CPU oracle,
+through the C ABI.  Index maps bit-exact; FP64 outputs within 1e-12 normwise."""
+import numpy as np
+import pytest
+
+from hpcg_inputs import normal, uniform
+from oracle import OracleProblem
+from tests.gpu_util import TOL64, dev, host, need_gpu, normwise
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((16, 16, 16), 4), ((8, 12, 16), 3), ((2, 2, 2), 1), ((3, 5, 7), 1), ((6, 4, 10), 2), ((64, 32, 48), 4),
+         ((34, 18, 66), 2)]
+
+
+def _pair(dims, levels, kappa=None):
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    g = HpcgProblem(*dims, levels=levels, kappa=None if kappa is None else dev(kappa))
+    o = OracleProblem(*dims, levels=levels, kappa=kappa)
+    return g, o
+
+
+@pytest.mark.parametrize("dims,levels", CASES)
+def test_setup_maps_bit_exact(dims, levels):
+    g, o = _pair(dims, levels)
+    for l in range(levels):
+        assert g.level_dims(l) == o.dims(l)
+        np.testing.assert_array_equal(g.get_colors(l).cpu().numpy(), o.colors(l))
+        np.testing.assert_array_equal(g.get_row_nnz(l).cpu().numpy(), o.row_nnz(l))
+        if l < levels - 1:
+            np.testing.assert_array_equal(g.get_f2c(l).cpu().numpy(), o.f2c(l))
+    np.testing.assert_array_equal(host(g.get_rhs()), o.rhs())
+
+
+@pytest.mark.parametrize("dims,levels", CASES)
+@pytest.mark.parametrize("with_kappa", [False, True])
+def test_spmv(dims, levels, with_kappa):
+    n = int(np.prod(dims))
+    kappa = uniform(n, 0.0, 1.0, 4) if with_kappa else None
+    g, o = _pair(dims, levels, kappa)
+    for l in range(levels):
+        x = normal(o.n(l), 10 + l)
+        y = host(g.spmv(dev(x), level=l))
+        assert normwise(y, o.spmv(x, l)) <= TOL64
+
+
+@pytest.mark.parametrize("dims,levels", CASES)
+@pytest.mark.parametrize("with_kappa", [False, True])
+def test_colour_steps_and_sweep(dims, levels, with_kappa):
+    n = int(np.prod(dims))
+    kappa = uniform(n, 0.0, 1.0, 4) if with_kappa else None
+    g, o = _pair(dims, levels, kappa)
+    for l in range(levels):
+        r = normal(o.n(l), 20 + l)
+        z0 = normal(o.n(l), 30 + l)
+        zg = dev(z0)
+        zo = z0.copy()
+        for k in list(range(8)) + list(range(7, -1, -1)):
+            g.rbgs_color(dev(r), zg, k, level=l)
+            zo = o.rbgs_color_step(k, r, zo, l)
+            assert normwise(host(zg), zo) <= TOL64, (l, k)
+        # one whole smoother application (forward then backward colours)
+        zs = dev(z0)
+        g.rbgs(dev(r), zs, level=l)
+        assert normwise(host(zs), o.rbgs(r, z0, l)) <= TOL64
+
+
+@pytest.mark.parametrize("dims,levels", [c for c in CASES if c[1] > 1])
+@pytest.mark.parametrize("with_kappa", [False, True])
+def test_restrict_residual_and_prolong(dims, levels, with_kappa):
+    n = int(np.prod(dims))
+    kappa = uniform(n, 0.0, 1.0, 4) if with_kappa else None
+    g, o = _pair(dims, levels, kappa)
+    for l in range(levels - 1):
+        r = normal(o.n(l), 40 + l)
+        z = normal(o.n(l), 50 + l)
+        rc = host(g.restrict_residual(dev(r), dev(z), level=l))
+        ref = o.restrict(r - o.spmv(z, l), l)
+        assert normwise(rc, ref) <= TOL64
+        zc = normal(o.n(l + 1), 60 + l)
+        zg = dev(z)
+        g.prolong_add(dev(zc), zg, level=l)
+        assert normwise(host(zg), o.prolong_add(zc, z, l)) <= TOL64
+
+
+@pytest.mark.parametrize("dims,levels", CASES)
+@pytest.mark.parametrize("with_kappa", [False, True])
+def test_vcycle_fp64(dims, levels, with_kappa):
+    n = int(np.prod(dims))
+    kappa = uniform(n, 0.0, 1.0, 4) if with_kappa else None
+    g, o = _pair(dims, levels, kappa)
+    r = normal(n, 70)
+    z = host(g.mg_vcycle(dev(r)))
+    assert normwise(z, o.mg(r)) <= TOL64
+
+
+def test_dot_and_waxpby():
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    g = HpcgProblem(16, 16, 16, levels=4)
+    for n in [0, 1, 255, 256, 257, 4096, 1000003]:
+        a, b = normal(n, 1), normal(n, 2)
+        d = host(g.dot(dev(a), dev(b)))[0]
+        ref = float(np.dot(a, b)) if n else 0.0
+        assert abs(d - ref) <= 1e-13 * max(np.abs(a) @ np.abs(b), 1e-300)
+        w = host(g.waxpby(1.5, dev(a), -0.25, dev(b)))
+        np.testing.assert_allclose(w, 1.5 * a - 0.25 * b, rtol=0, atol=1e-15 * (1 + np.abs(w).max(initial=0.0)))
+
+
+def test_dot_is_deterministic():
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    g = HpcgProblem(16, 16, 16, levels=4)
+    a, b = dev(normal(3000017, 5)), dev(normal(3000017, 6))
+    vals = {float(host(g.dot(a, b))[0]) for _ in range(5)}
+    assert len(vals) == 1
