@@ -194,6 +194,40 @@ int hpcg_batch_offsets(hpcg_handle h, long *offsets_host);
 int hpcg_pcg_solve_batch(hpcg_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol,
                          hpcg_stats *stats, void *stream);
 
+/* --- allocation-free V-cycle ---------------------------------------------------------- */
+/* No counterpart in the paper: a convenience for callers that cannot allocate
+ * device memory when they need the preconditioner (for example code running
+ * during a CUDA graph capture under a strict allocator, plug-ins inside a host
+ * application that owns all device allocations, or real-time loops that forbid
+ * allocation after start-up).
+ *
+ * z = M r for an nx x ny x nz grid with `levels` levels, exactly the FP64
+ * V-cycle of hpcg_mg_vcycle with default options (one symmetric smoother
+ * application before and after each coarse correction, no kappa field), but
+ * without a handle: r_dev and z_dev (FP64 [nx*ny*nz], device, caller-owned, not
+ * overlapping) are the only buffers it touches besides a fixed device array of
+ * HPCG_NOALLOC_SCRATCH_BYTES inside the library, which holds the level tables
+ * and the coarse-level vectors.  That array is static: every GPU that loads the
+ * library keeps it until the process exits, and the call itself allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *  - Size limit: the coarse levels need 16 bytes per coarse row (sum over levels
+ *    1..levels-1 of (nx>>l)(ny>>l)(nz>>l)) plus under 4 KiB of tables and alignment
+ *    padding; larger problems
+ *    are rejected with HPCG_ERR_NO_WORKSPACE before any GPU work.  192^3 with 4
+ *    levels fits.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and leaves its contents behind; the
+ *    V-cycle zeroes each coarse correction itself before use, so stale contents
+ *    never leak into a result.  Calls whose GPU work overlaps (different
+ *    streams, or host threads without ordering) race on the array: serialise
+ *    them on one stream.
+ * Errors: INVALID_ARG for null or identical pointers and for the size rules of
+ * hpcg_setup; NO_WORKSPACE beyond the size limit; CUDA for a failed launch. */
+#define HPCG_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const double *r_dev, double *z_dev, void *stream);
+
 /* --- diagnostics ------------------------------------------------------------------ */
 const char *hpcg_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (thread-unsafe). */

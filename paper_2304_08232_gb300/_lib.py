@@ -52,6 +52,7 @@ SIGNATURES = {
     "hpcg_setup_batch": (_i, [_i, ctypes.POINTER(_i), _i, _i, ctypes.POINTER(_vp)]),
     "hpcg_batch_offsets": (_i, [_vp, ctypes.POINTER(_l)]),
     "hpcg_pcg_solve_batch": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
+    "hpcg_mg_vcycle_noalloc": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
     "hpcg_strerror": (ctypes.c_char_p, [_i]),
     "hpcg_last_cuda_error": (ctypes.c_char_p, []),
     "hpcg_launch_count": (_l, []),

@@ -847,3 +847,115 @@ const char *hpcg_last_cuda_error(void) { return g_last_cuda_error; }
 long hpcg_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free V-cycle.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// preconditioner application: code running while a CUDA graph is being
+// captured under a strict allocator, plug-ins living inside a host
+// application that owns every device allocation, or real-time loops that
+// forbid allocation after start-up.  hpcg_mg_vcycle_noalloc serves them: it
+// takes only the input r and the output z, and keeps everything else (the
+// level tables and the coarse-level vectors r_l, z_l of levels 1..L-1) in the
+// fixed device array below, which every GPU that loads this library holds
+// until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HPCG_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch per device.  In host code the array's
+// name only stands for the symbol, so its device address is looked up once per
+// device, with that device current, by cudaGetSymbolAddress.
+static void *g_noalloc_base[64];
+static std::mutex g_noalloc_mu;
+
+static int noalloc_base(void **out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return HPCG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return HPCG_OK;
+}
+
+// Writes the one-instance level tables of an nx x ny x nz hierarchy.
+__global__ void k_noalloc_tables(int nx, int ny, int nz, int levels, Inst *__restrict__ tabs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int l = 0; l < levels; ++l) {
+    Inst g;
+    g.nx = nx >> l;
+    g.ny = ny >> l;
+    g.nz = nz >> l;
+    g.n = (long)g.nx * g.ny * g.nz;
+    g.off = 0;
+    g.blk_full = 0;
+    g.blk_half = 0;
+    g.blk_red = 0;
+    long b = (g.n + (long)kRedThreads * kRedItems - 1) / ((long)kRedThreads * kRedItems);
+    g.nred = (int)(b < 1 ? 1 : (b > kMaxRedBlocksPerInst ? kMaxRedBlocksPerInst : b));
+    g.pad = 0;
+    tabs[l] = g;
+  }
+}
+
+extern "C" int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const double *r_dev, double *z_dev, void *stream) {
+  if (!r_dev || !z_dev || r_dev == z_dev) return HPCG_ERR_INVALID_ARG;
+  TRY(validate_dims(nx, ny, nz, levels));
+  // scratch layout: level tables, then r_l and z_l of every coarse level
+  const size_t tab_bytes = align256(sizeof(Inst) * kMaxLevels);
+  size_t need = tab_bytes;
+  size_t off_r[kMaxLevels] = {0}, off_z[kMaxLevels] = {0};
+  for (int l = 1; l < levels; ++l) {
+    const size_t nl = (size_t)(nx >> l) * (size_t)(ny >> l) * (size_t)(nz >> l);
+    off_r[l] = need;
+    need = align256(need + sizeof(double) * nl);
+    off_z[l] = need;
+    need = align256(need + sizeof(double) * nl);
+  }
+  if (need > (size_t)HPCG_NOALLOC_SCRATCH_BYTES) return HPCG_ERR_NO_WORKSPACE;
+  void *base_v = nullptr;
+  TRY(noalloc_base(&base_v));
+  char *base = (char *)base_v;
+  cudaStream_t s = (cudaStream_t)stream;
+  Inst *tabs = (Inst *)base;
+  k_noalloc_tables<<<1, 32, 0, s>>>(nx, ny, nz, levels, tabs);
+  CKL("k_noalloc_tables");
+  double *rl[kMaxLevels], *zl[kMaxLevels];
+  int nfull[kMaxLevels], nhalf[kMaxLevels], nred[kMaxLevels];
+  for (int l = 0; l < levels; ++l) {
+    const int a = nx >> l, b = ny >> l, c = nz >> l;
+    nfull[l] = tiles_of(a, b, c);
+    nhalf[l] = tiles_of(half_up(a), half_up(b), half_up(c));
+    nred[l] = red_blocks((long)a * b * c);
+    rl[l] = l == 0 ? const_cast<double *>(r_dev) : (double *)(base + off_r[l]);
+    zl[l] = l == 0 ? z_dev : (double *)(base + off_z[l]);
+  }
+  // one symmetric smoother application: colours 0..7 then 6..0 (the repeat of
+  // colour 7 returns the same bits and is left out, as in hpcg_mg_vcycle)
+  static const int kSeq[15] = {0, 1, 2, 3, 4, 5, 6, 7, 6, 5, 4, 3, 2, 1, 0};
+  const dim3 blk(kTileX, kTileY);
+  for (int l = 0; l < levels; ++l) {
+    k_zero_inst<double><<<nred[l], kRedThreads, 0, s>>>(tabs + l, 1, zl[l], nullptr);
+    CKL("k_zero_inst");
+    for (int k : kSeq) {
+      k_gs_color<double><<<nhalf[l], blk, 0, s>>>(tabs + l, 1, k & 1, (k >> 1) & 1, (k >> 2) & 1, rl[l], zl[l], nullptr, nullptr);
+      CKL("k_gs_color");
+    }
+    if (l == levels - 1) break;
+    k_restrict_residual<double><<<nfull[l + 1], blk, 0, s>>>(tabs + l, tabs + l + 1, 1, rl[l], zl[l], rl[l + 1], nullptr, nullptr);
+    CKL("k_restrict_residual");
+  }
+  for (int l = levels - 2; l >= 0; --l) {
+    k_prolong_add<double><<<nfull[l + 1], blk, 0, s>>>(tabs + l, tabs + l + 1, 1, zl[l + 1], zl[l], nullptr);
+    CKL("k_prolong_add");
+    for (int k : kSeq) {
+      k_gs_color<double><<<nhalf[l], blk, 0, s>>>(tabs + l, 1, k & 1, (k >> 1) & 1, (k >> 2) & 1, rl[l], zl[l], nullptr, nullptr);
+      CKL("k_gs_color");
+    }
+  }
+  return HPCG_OK;
+}
