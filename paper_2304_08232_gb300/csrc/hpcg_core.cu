@@ -11,81 +11,20 @@
 #include <vector>
 
 #include "hpcg.h"
+#include "hpcg_ctx.h"
 #include "hpcg_kernels.cuh"
 
 using namespace hpcg;
 
 // ---------------------------------------------------------------------------
-// error plumbing
-static char g_last_cuda_error[256] = "no error";
-static std::atomic<long> g_launches{0};
+// error plumbing (declared in hpcg_ctx.h)
+char g_last_cuda_error[256] = "no error";
+std::atomic<long> g_launches{0};
 
-static int cuda_fail(cudaError_t e, const char *what) {
+int cuda_fail(cudaError_t e, const char *what) {
   snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", what, cudaGetErrorString(e));
   return HPCG_ERR_CUDA;
 }
-#define CK(call)                                          \
-  do {                                                    \
-    cudaError_t e_ = (call);                              \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
-  } while (0)
-#define CKL(what)                                         \
-  do {                                                    \
-    g_launches.fetch_add(1, std::memory_order_relaxed);   \
-    cudaError_t e_ = cudaGetLastError();                  \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what);    \
-  } while (0)
-#define TRY(x)              \
-  do {                      \
-    int rc_ = (x);          \
-    if (rc_ != HPCG_OK) return rc_; \
-  } while (0)
-
-static inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
-
-// ---------------------------------------------------------------------------
-struct LevelData {
-  std::vector<Inst> inst;  // host copy
-  LevelTab tab{};
-  long n = 0;
-  // workspace offsets (bytes)
-  size_t o_tab = 0, o_r = 0, o_z = 0, o_r32 = 0, o_z32 = 0, o_kap = 0, o_invd = 0, o_kap32 = 0, o_invd32 = 0;
-  // device pointers (valid once a workspace is bound)
-  double *r = nullptr, *z = nullptr, *kap = nullptr, *invd = nullptr;
-  float *r32 = nullptr, *z32 = nullptr, *kap32 = nullptr, *invd32 = nullptr;
-};
-
-struct GraphCache {
-  cudaGraphExec_t exec = nullptr;
-  const void *key[4] = {nullptr, nullptr, nullptr, nullptr};
-  long kernels = 0;
-};
-
-struct hpcg_ctx {
-  int batch = 0;  // 0: single grid, 1: batch of grids
-  hpcg_options opt{};
-  int levels = 0;
-  int count = 1;
-  bool has_kappa = false;
-  const double *kappa_pending = nullptr;
-  LevelData lv[kMaxLevels];
-  // workspace
-  char *ws = nullptr;
-  size_t ws_bytes = 0, need = 0;
-  bool ws_owned = false;
-  bool ready = false;
-  size_t o_st = 0, o_hist = 0, o_part = 0, o_out = 0, o_cg = 0;
-  size_t npart = 0;
-  CgState *st = nullptr;
-  double *hist = nullptr, *part = nullptr, *dout = nullptr;
-  double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_ap = nullptr;
-  // multi-RHS region (sized by opt.max_rhs)
-  size_t o_multi = 0, multi_bytes = 0;
-  cudaStream_t cap = nullptr;
-  GraphCache g_iter;
-  int device = 0;
-  std::mutex mu;
-};
 
 // ---------------------------------------------------------------------------
 static int validate_dims(int nx, int ny, int nz, int levels) {
@@ -98,7 +37,7 @@ static int validate_dims(int nx, int ny, int nz, int levels) {
   return HPCG_OK;
 }
 
-static int red_blocks(long n) {
+int red_blocks(long n) {
   long b = (n + (long)kRedThreads * kRedItems - 1) / ((long)kRedThreads * kRedItems);
   if (b < 1) b = 1;
   if (b > kMaxRedBlocksPerInst) b = kMaxRedBlocksPerInst;
@@ -172,13 +111,13 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
   }
   h->multi_bytes = 0;
   if (h->opt.max_rhs > 0 && h->batch == 0) {
-    // multi-RHS: CG vectors r z p ap (n0 x R), level vectors r z (l >= 1),
-    // per-RHS partial sums, states and history
-    size_t R = (size_t)h->opt.max_rhs;
-    size_t b = align256(sizeof(double) * 4 * (size_t)n0 * R);
-    for (int l = 1; l < h->levels; ++l) b += align256(sizeof(double) * 2 * (size_t)h->lv[l].n * R);
-    b += align256(sizeof(double) * R * (size_t)(h->lv[0].tab.nblk_full + kMaxRedBlocksPerInst + 64));
-    b += align256(sizeof(CgState) * R) + align256(sizeof(double) * R * kHistoryCap);
+    // multi-RHS region (carved by hpcg_multi.cu for the actual nrhs <= max_rhs):
+    // interleaved X B r z p Ap (6 n0 R), level vectors r z (l >= 1), per-rhs
+    // partials of the fixed reduction grid, states and histories
+    const size_t R = (size_t)h->opt.max_rhs;
+    size_t b = 6 * align256(sizeof(double) * (size_t)n0 * R);
+    for (int l = 1; l < h->levels; ++l) b += 2 * align256(sizeof(double) * (size_t)h->lv[l].n * R);
+    b += align256(sizeof(double) * R * 1184) + align256(sizeof(CgState) * R) + align256(sizeof(double) * R * kHistoryCap);
     h->o_multi = take(b);
     h->multi_bytes = b;
   }
@@ -221,13 +160,17 @@ static int bind(hpcg_ctx *h, char *ws, size_t bytes, bool owned) {
     cudaGraphExecDestroy(h->g_iter.exec);
     h->g_iter = GraphCache{};
   }
+  if (h->g_multi.exec) {  // captured with pointers into the previous workspace
+    cudaGraphExecDestroy(h->g_multi.exec);
+    h->g_multi = GraphCache{};
+  }
   h->ready = true;
   return HPCG_OK;
 }
 
 static int set_kappa_impl(hpcg_ctx *h, const double *kappa, cudaStream_t s);
 
-static int ensure_ready(hpcg_ctx *h, cudaStream_t s) {
+int ensure_ready(hpcg_ctx *h, cudaStream_t s) {
   if (!h->ready) {
     char *p = nullptr;
     cudaError_t e = cudaMalloc(&p, h->need);
@@ -245,7 +188,7 @@ static int ensure_ready(hpcg_ctx *h, cudaStream_t s) {
   return HPCG_OK;
 }
 
-static inline int grid_for(long n) {
+int grid_for(long n) {
   long b = (n + 255) / 256;
   if (b > 152L * 16) b = 152L * 16;
   if (b < 1) b = 1;
@@ -646,6 +589,7 @@ int hpcg_destroy(hpcg_handle h) {
   if (!h) return HPCG_ERR_INVALID_ARG;
   if (h->ready) cudaDeviceSynchronize();
   if (h->g_iter.exec) cudaGraphExecDestroy(h->g_iter.exec);
+  if (h->g_multi.exec) cudaGraphExecDestroy(h->g_multi.exec);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ws_owned && h->ws) cudaFree(h->ws);
   delete h;
@@ -820,12 +764,6 @@ int hpcg_pcg_backward(hpcg_handle h, const double *x_dev, const double *grad_x_d
     CKL("k_grad_kappa");
   }
   return rc;
-}
-
-int hpcg_pcg_solve_multi(hpcg_handle h, int nrhs, const double *B_dev, double *X_dev, int max_iters, double rel_tol,
-                         hpcg_stats *stats, void *stream) {
-  (void)h; (void)nrhs; (void)B_dev; (void)X_dev; (void)max_iters; (void)rel_tol; (void)stats; (void)stream;
-  return HPCG_ERR_UNSUPPORTED;
 }
 
 const char *hpcg_strerror(int status) {

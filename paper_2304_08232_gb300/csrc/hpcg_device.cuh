@@ -1,0 +1,144 @@
+// hpcg_device.cuh -- inline device helpers shared by the kernel files:
+// matrix-free neighbour sums of the 27-point operator (Sections II-B/C) and
+// deterministic block reductions.
+#pragma once
+#include "hpcg_internal.cuh"
+
+namespace hpcg {
+
+// Sum of the 26 neighbours of (x,y,z) that lie inside the grid, in ascending
+// column order.  v points at the grid's first row.
+template <typename T>
+__device__ __forceinline__ T nbr_sum26(const T *__restrict__ v, int x, int y, int z, int nx, int ny, int nz) {
+  T s = T(0);
+  const long sxy = (long)nx * ny;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int zz = z + dz;
+    if (zz < 0 || zz >= nz) continue;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = y + dy;
+      if (yy < 0 || yy >= ny) continue;
+      const long base = (long)zz * sxy + (long)yy * nx;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = x + dx;
+        if (xx < 0 || xx >= nx) continue;
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        s += __ldg(v + base + xx);
+      }
+    }
+  }
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T diag_of(const T *__restrict__ kap, long gi) {
+  return kap ? T(26) + kap[gi] : T(26);
+}
+
+template <typename T>
+__device__ __forceinline__ T inv_diag_of(const T *__restrict__ invd, long gi) {
+  return invd ? invd[gi] : T(1) / T(26);
+}
+
+// Deterministic block sum (fixed shuffle tree, fixed warp order); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int warp = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+  if ((tid & 31) == 0) sh[warp] = v;
+  (void)lane;
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0)
+    for (int w = 0; w < nwarps; ++w) s += sh[w];
+  __syncthreads();
+  return s;
+}
+
+// Fixed-order sum of partials[first .. first+cnt) inside one block; valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double *__restrict__ partials, int first, int cnt, double *sh) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) s += partials[first + k];
+  return block_sum(s, sh);
+}
+
+enum FinKind { FIN_NORM0 = 0, FIN_RTZ = 1, FIN_PAP = 2, FIN_NORM = 3, FIN_OUT = 4 };
+
+// CG scalar update of one instance from a finished reduction s (thread 0 only):
+//  FIN_NORM0: normr0 = sqrt(s)            (start of the solve)
+//  FIN_RTZ:   rtz' = s; beta = rtz'/rtz   (after z = M r)
+//  FIN_PAP:   alpha = rtz / s             (after Ap = A p; breakdown check)
+//  FIN_NORM:  normr = sqrt(s); history; convergence and stall tests
+// hist points at this instance's history row (nullable).
+template <int Kind>
+__device__ __forceinline__ void fin_apply(CgState &c, double s, double *hist) {
+  if (Kind == FIN_NORM0) {
+    c.normr0 = sqrt(s);
+    c.normr = c.normr0;
+    c.best = c.normr0;
+    if (!(c.normr0 > 0.0) || !isfinite(c.normr0)) {
+      c.done = 1;
+      c.converged = (c.normr0 == 0.0);
+      c.status = (c.normr0 == 0.0) ? HPCG_OK : HPCG_ERR_BREAKDOWN;
+    }
+  } else if (Kind == FIN_RTZ) {
+    if (c.restart) {
+      c.first = 1;
+      c.restart = 0;
+      c.restarts += 1;
+    }
+    if (c.first) {
+      c.beta = 0.0;
+    } else {
+      c.beta = s / c.rtz;
+    }
+    c.rtz = s;
+    if (!isfinite(s)) {
+      c.done = 1;
+      c.status = HPCG_ERR_BREAKDOWN;
+    }
+  } else if (Kind == FIN_PAP) {
+    c.pAp = s;
+    if (!(s > 0.0) || !isfinite(s)) {
+      c.done = 1;
+      c.status = HPCG_ERR_BREAKDOWN;
+      c.alpha = 0.0;
+    } else {
+      c.alpha = c.rtz / s;
+    }
+    c.first = 0;
+  } else if (Kind == FIN_NORM) {
+    c.normr = sqrt(s);
+    const double rel = c.normr / c.normr0;
+    if (hist && c.iter < kHistoryCap) hist[c.iter] = rel;
+    c.iter += 1;
+    if (!isfinite(rel)) {
+      c.done = 1;
+      c.status = HPCG_ERR_BREAKDOWN;
+    } else if (c.tol > 0.0 && rel <= c.tol) {
+      c.done = 1;
+      c.converged = 1;
+    } else if (c.iter >= c.max_iters) {
+      c.done = 1;
+    } else if (c.mixed) {
+      // stall test of the mixed-precision outer loop: no 1% progress over the
+      // best residual for 3 iterations -> replace r by b - A x next iteration
+      if (c.normr < 0.99 * c.best) {
+        c.best = c.normr;
+        c.stall = 0;
+      } else if (++c.stall >= 3) {
+        c.restart = 1;
+        c.stall = 0;
+        c.best = c.normr;
+      }
+    }
+  }
+}
+
+}  // namespace hpcg
