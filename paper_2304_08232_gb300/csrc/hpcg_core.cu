@@ -13,6 +13,7 @@
 #include "hpcg.h"
 #include "hpcg_ctx.h"
 #include "hpcg_kernels.cuh"
+#include "hpcg_lines.cuh"
 
 using namespace hpcg;
 
@@ -42,6 +43,64 @@ int red_blocks(long n) {
   if (b < 1) b = 1;
   if (b > kMaxRedBlocksPerInst) b = kMaxRedBlocksPerInst;
   return (int)b;
+}
+
+static int nch_supported(int need) {
+  static const int avail[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16};
+  for (int a : avail)
+    if (a >= need) return a;
+  return 0;
+}
+
+static void set_line_prefixes(LevelData &L) {
+  int br = 0, bl = 0;
+  for (Inst &g : L.inst) {
+    g.blk_row = br;
+    g.nrow = row_blocks(g.ny, g.nz, L.tab.row_lpc, L.tab.row_zc);
+    g.blk_line = bl;
+    g.nline = line_blocks(g.ny, g.nz, L.tab.line_lpc, L.tab.line_zc);
+    br += g.nrow;
+    bl += g.nline;
+  }
+  L.tab.nblk_row = br;
+  L.tab.nblk_line = bl;
+}
+
+// Launch shape of the line kernels of a level: the largest z-chunk (longest
+// reuse of plane sums) and lines per block that still give at least two blocks
+// per SM over all instances (152 SMs), else the shape with the most blocks.
+static void choose_line_params(LevelData &L) {
+  int nxm = 0;
+  for (const Inst &g : L.inst) nxm = std::max(nxm, g.nx);
+  L.tab.nch = nch_supported((nxm + 31) / 32);
+  const int target = 2 * 152;
+  auto pick = [&](bool lines_of_class, int *lpc_out, int *zc_out) {
+    static const int lpcs[] = {8, 4, 2, 1};
+    static const int zcs[] = {16, 8, 4, 2, 1};
+    int best_lpc = 1, best_zc = 1;
+    long best_blocks = -1;
+    for (int zc : zcs)
+      for (int lpc : lpcs) {
+        long blocks = 0;
+        for (const Inst &g : L.inst)
+          blocks += lines_of_class ? line_blocks(g.ny, g.nz, lpc, zc) : row_blocks(g.ny, g.nz, lpc, zc);
+        if (blocks >= target && lpc >= 2) {
+          *lpc_out = lpc;
+          *zc_out = zc;
+          return;
+        }
+        if (blocks > best_blocks) {
+          best_blocks = blocks;
+          best_lpc = lpc;
+          best_zc = zc;
+        }
+      }
+    *lpc_out = best_lpc;
+    *zc_out = best_zc;
+  };
+  pick(false, &L.tab.row_lpc, &L.tab.row_zc);
+  pick(true, &L.tab.line_lpc, &L.tab.line_zc);
+  set_line_prefixes(L);
 }
 
 // Builds the instance tables and the workspace layout.
@@ -81,12 +140,13 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
     L.tab.nblk_half = bh;
     L.tab.nblk_red = br;
     L.tab.n = rows;
+    choose_line_params(L);
   }
   for (int l = 0; l < h->levels; ++l) h->lv[l].o_tab = take(sizeof(Inst) * h->count);
   h->o_st = take(sizeof(CgState) * h->count);
   h->o_hist = take(sizeof(double) * (size_t)kHistoryCap * h->count);
   const LevelData &L0 = h->lv[0];
-  h->npart = (size_t)std::max(std::max(L0.tab.nblk_full, L0.tab.nblk_red), kRawDotBlocks) + 64;
+  h->npart = (size_t)std::max(std::max(std::max(L0.tab.nblk_full, L0.tab.nblk_red), L0.tab.nblk_row), kRawDotBlocks) + 64;
   h->o_part = take(sizeof(double) * h->npart);
   h->o_out = take(sizeof(double) * (h->count + 64));
   const long n0 = L0.n;
@@ -249,18 +309,81 @@ const double *invd_of<double>(const LevelData &L, bool has) { return has ? L.inv
 template <>
 const float *invd_of<float>(const LevelData &L, bool has) { return has ? L.invd32 : nullptr; }
 
+template <typename T, int NCH>
+static void launch_gs_lines(const LevelData &L, int count, int py, int pz, int pa, int steps, const T *r, T *z, const T *invd,
+                            const CgState *st, cudaStream_t s) {
+  k_gs_lines<T, NCH><<<L.tab.nblk_line, dim3(32, L.tab.line_lpc), 0, s>>>(L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa,
+                                                                         steps, r, z, invd, st);
+}
+
+// `steps` colour steps on the lines of class (py, pz), alternating x parity from pa.
 template <typename T>
-static int enqueue_colour(hpcg_ctx *h, int l, int k, const T *r, T *z, cudaStream_t s, const CgState *st) {
+static int enqueue_line_steps(hpcg_ctx *h, int l, int py, int pz, int pa, int steps, const T *r, T *z, cudaStream_t s,
+                              const CgState *st) {
   const LevelData &L = h->lv[l];
-  k_gs_color<T><<<L.tab.nblk_half, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, k & 1, (k >> 1) & 1, (k >> 2) & 1, r, z,
-                                                                 invd_of<T>(L, h->has_kappa), st);
-  CKL("k_gs_color");
+  const T *invd = invd_of<T>(L, h->has_kappa);
+  switch (L.tab.nch) {
+#define HPCG_GS_CASE(N) \
+  case N: launch_gs_lines<T, N>(L, h->count, py, pz, pa, steps, r, z, invd, st, s); break;
+    HPCG_GS_CASE(1) HPCG_GS_CASE(2) HPCG_GS_CASE(3) HPCG_GS_CASE(4) HPCG_GS_CASE(5) HPCG_GS_CASE(6)
+    HPCG_GS_CASE(7) HPCG_GS_CASE(8) HPCG_GS_CASE(10) HPCG_GS_CASE(12) HPCG_GS_CASE(16)
+#undef HPCG_GS_CASE
+    default: {
+      // lines longer than the register window: one launch per colour step
+      for (int k = 0; k < steps; ++k) {
+        const int px = (k & 1) ? 1 - pa : pa;
+        k_gs_color<T><<<L.tab.nblk_half, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, px, py, pz, r, z, invd, st);
+        CKL("k_gs_color");
+      }
+      return HPCG_OK;
+    }
+  }
+  CKL("k_gs_lines");
   return HPCG_OK;
 }
 
 template <typename T>
+static int enqueue_colour(hpcg_ctx *h, int l, int k, const T *r, T *z, cudaStream_t s, const CgState *st) {
+  return enqueue_line_steps<T>(h, l, (k >> 1) & 1, (k >> 2) & 1, k & 1, 1, r, z, s, st);
+}
+
+// The smoother's colour sequence grouped into runs of one line class: the
+// colours 2m, 2m+1 of a run share (y, z) parities and alternate in x parity.
+template <typename T>
 static int enqueue_smoother(hpcg_ctx *h, int l, const T *r, T *z, int sweeps, cudaStream_t s, const CgState *st) {
-  for (int k : phase_sequence(sweeps, h->opt.symmetric)) TRY(enqueue_colour<T>(h, l, k, r, z, s, st));
+  const std::vector<int> seq = phase_sequence(sweeps, h->opt.symmetric);
+  size_t i = 0;
+  while (i < seq.size()) {
+    size_t j = i + 1;
+    while (j < seq.size() && (seq[j] >> 1) == (seq[i] >> 1)) ++j;
+    const int k = seq[i];
+    TRY(enqueue_line_steps<T>(h, l, (k >> 1) & 1, (k >> 2) & 1, k & 1, (int)(j - i), r, z, s, st));
+    i = j;
+  }
+  return HPCG_OK;
+}
+
+// y = A x (Mode 0) or y = b - A x (Mode 1) on level l; optional p.Ap partials
+// (then finalize with stencil mode 2).
+template <typename T, int Mode>
+static int enqueue_spmv(hpcg_ctx *h, int l, const T *x, const T *b, T *y, const T *kap, double *partials, const CgState *st,
+                        cudaStream_t s) {
+  const LevelData &L = h->lv[l];
+  const dim3 blk(32, L.tab.row_lpc);
+  switch (L.tab.nch) {
+#define HPCG_SP_CASE(N)                                                                                                          \
+  case N:                                                                                                                        \
+    k_spmv_lines<T, N, Mode><<<L.tab.nblk_row, blk, 0, s>>>(L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, \
+                                                            partials, st);                                                     \
+    break;
+    HPCG_SP_CASE(1) HPCG_SP_CASE(2) HPCG_SP_CASE(3) HPCG_SP_CASE(4) HPCG_SP_CASE(5) HPCG_SP_CASE(6)
+    HPCG_SP_CASE(7) HPCG_SP_CASE(8) HPCG_SP_CASE(10) HPCG_SP_CASE(12) HPCG_SP_CASE(16)
+#undef HPCG_SP_CASE
+    default:  // lines longer than the register window: one thread per row (partials per 32x8 tile)
+      k_spmv<T, Mode><<<L.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, x, b, y, kap, partials, st);
+      break;
+  }
+  CKL("k_spmv_lines");
   return HPCG_OK;
 }
 
@@ -349,9 +472,7 @@ static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_ite
   CK(cudaMemcpyAsync(h->st, init.data(), sizeof(CgState) * h->count, cudaMemcpyHostToDevice, s));
   const LevelData &L0 = h->lv[0];
   // r = b - A x
-  k_spmv<double, 1><<<L0.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L0.tab.inst, h->count, x, b, h->cg_r,
-                                                                      h->has_kappa ? L0.kap : nullptr, nullptr, nullptr);
-  CKL("k_spmv(residual)");
+  TRY((enqueue_spmv<double, 1>(h, 0, x, b, h->cg_r, h->has_kappa ? L0.kap : nullptr, nullptr, nullptr, s)));
   k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_r, h->part, h->st);
   CKL("k_dot_partial");
   k_finalize<FIN_NORM0><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
@@ -376,10 +497,8 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   CKL("k_finalize<RTZ>");
   k_update_p<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_z, h->cg_p, h->st);  // p = z + beta p
   CKL("k_update_p");
-  k_spmv<double, 0><<<L0.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L0.tab.inst, h->count, h->cg_p, nullptr, h->cg_ap, kap,
-                                                                      h->part, h->st);  // Ap, p.Ap
-  CKL("k_spmv");
-  k_finalize<FIN_PAP><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 1, h->st, h->hist, nullptr);
+  TRY((enqueue_spmv<double, 0>(h, 0, h->cg_p, nullptr, h->cg_ap, kap, h->part, h->st, s)));  // Ap, p.Ap partials
+  k_finalize<FIN_PAP><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, L0.tab.nch ? 2 : 1, h->st, h->hist, nullptr);
   CKL("k_finalize<PAP>");
   k_update_xr<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r, h->part, h->st);
   CKL("k_update_xr");
@@ -660,9 +779,7 @@ int hpcg_spmv(hpcg_handle h, int level, const double *x_dev, double *y_dev, void
   cudaStream_t s = (cudaStream_t)stream;
   TRY(ensure_ready(h, s));
   const LevelData &L = h->lv[level];
-  k_spmv<double, 0><<<L.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, x_dev, nullptr, y_dev,
-                                                                     h->has_kappa ? L.kap : nullptr, nullptr, nullptr);
-  CKL("k_spmv");
+  TRY((enqueue_spmv<double, 0>(h, level, x_dev, nullptr, y_dev, h->has_kappa ? L.kap : nullptr, nullptr, nullptr, s)));
   return HPCG_OK;
 }
 
@@ -833,6 +950,7 @@ __global__ void k_noalloc_tables(int nx, int ny, int nz, int levels, Inst *__res
     g.blk_full = 0;
     g.blk_half = 0;
     g.blk_red = 0;
+    g.blk_row = g.nrow = g.blk_line = g.nline = 0;
     long b = (g.n + (long)kRedThreads * kRedItems - 1) / ((long)kRedThreads * kRedItems);
     g.nred = (int)(b < 1 ? 1 : (b > kMaxRedBlocksPerInst ? kMaxRedBlocksPerInst : b));
     g.pad = 0;

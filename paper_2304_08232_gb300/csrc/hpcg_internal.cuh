@@ -31,6 +31,10 @@ struct Inst {
   int blk_half;   // first block in a launch over one colour class (half lattice)
   int blk_red;    // first block in a reduction launch
   int nred;       // reduction blocks of this grid
+  int blk_row;    // first block in a line launch over every x-line (one warp per line)
+  int nrow;       // blocks of this grid in that launch
+  int blk_line;   // first block in a line launch over the lines of one colour-line class
+  int nline;      // blocks of this grid in that launch
   int pad;
   long off;       // first row of this grid in the level's concatenated vectors
   long n;         // rows
@@ -40,9 +44,22 @@ struct Inst {
 struct LevelTab {
   const Inst *inst;  // device array [count]
   int count;
-  int nblk_full, nblk_half, nblk_red;
-  long n;            // rows over all instances
+  int nblk_full, nblk_half, nblk_red, nblk_row, nblk_line;
+  int row_lpc, row_zc;    // line launch over all lines: lines (warps) per block, z-planes per block
+  int line_lpc, line_zc;  // line launch over one line class: lines per block, updated planes per block
+  int nch;                // 32-wide x chunks per line (ceil(max nx / 32)); 0 = line kernels unavailable
+  long n;                 // rows over all instances
 };
+
+// Blocks of a line launch over every x-line of an nx x ny x nz grid.
+__host__ __device__ inline int row_blocks(int ny, int nz, int lpc, int zc) {
+  return ((ny + lpc - 1) / lpc) * ((nz + zc - 1) / zc);
+}
+// Blocks of a line launch over the lines of one colour-line class (y, z of fixed parities).
+__host__ __device__ inline int line_blocks(int ny, int nz, int lpc, int zc) {
+  const int hy = (ny + 1) / 2, hz = (nz + 1) / 2;
+  return ((hy + lpc - 1) / lpc) * ((hz + zc - 1) / zc);
+}
 
 // Device-resident CG scalars of one instance.
 struct CgState {
@@ -65,7 +82,11 @@ __device__ inline int find_inst(const Inst *__restrict__ tab, int count, int b) 
   int lo = 0, hi = count - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    int start = Which == 0 ? tab[mid].blk_full : (Which == 1 ? tab[mid].blk_half : tab[mid].blk_red);
+    int start = Which == 0 ? tab[mid].blk_full
+                : Which == 1 ? tab[mid].blk_half
+                : Which == 2 ? tab[mid].blk_red
+                : Which == 3 ? tab[mid].blk_row
+                             : tab[mid].blk_line;
     if (start <= b) lo = mid; else hi = mid - 1;
   }
   return lo;

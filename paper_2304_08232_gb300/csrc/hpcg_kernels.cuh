@@ -222,7 +222,10 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const Inst *__restrict
   const int ii = blockIdx.x;
   const Inst g = tab[ii];
   int first, cnt;
-  if (stencil) {
+  if (stencil == 2) {  // line SpMV blocking
+    first = g.blk_row;
+    cnt = g.nrow;
+  } else if (stencil == 1) {  // 32x8 tile blocking
     first = g.blk_full;
     cnt = tiles_of(g.nx, g.ny, g.nz);
   } else {
