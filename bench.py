@@ -123,6 +123,20 @@ def dist_env():
     return world, rank, local
 
 
+def tuned_shapes(prob):
+    """Launch shapes the library's autotuner picked, per level:
+    [row lines, row planes, colour-line lines, colour-line planes]."""
+    import ctypes
+    import torch
+    from paper_2304_08232_gb300 import _lib
+    lib = _lib.load()
+    buf = (ctypes.c_int * (4 * prob.levels))()
+    rc = lib.hpcg_autotune(prob.h, buf, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise RuntimeError("hpcg_autotune failed: %d" % rc)
+    return [list(buf[4 * l:4 * l + 4]) for l in range(prob.levels)]
+
+
 # ---------------------------------------------------------------------------
 def cpu_baseline(steps_iters=2, nx=NX, ny=NY, nz=NZ):
     """The CPU oracle (single thread, as it stands) on a bounded sample of the
@@ -139,6 +153,64 @@ def cpu_baseline(steps_iters=2, nx=NX, ny=NY, nz=NZ):
     return {"value": fl / (t2 - t1) / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
             "sample": "%d MG-PCG iterations at %dx%dx%d (CRS build %.1f s excluded)" % (steps_iters, nx, ny, nz, t1 - t0),
             "seconds": t2 - t1}
+
+
+def other_forms(dev, stream):
+    """Timings of the batched and differentiable forms (one run each)."""
+    import torch
+    from hpcg_inputs import differentiable_inputs, multi_rhs, normal, uneven_batch_dims
+    from paper_2304_08232_gb300 import HpcgBatch, HpcgProblem, hpcg_solve
+
+    def timed(fn):
+        fn()  # warm-up: graph capture, autotuning
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    res = {}
+    # (a) 32 right-hand sides ~ N(0,1) (seed 2) on 128^3, to 1e-8
+    n = 128 ** 3
+    g = HpcgProblem(128, 128, 128, levels=4, max_rhs=32, device=dev)
+    B = torch.as_tensor(multi_rhs(n, 32, seed=2), device=dev)
+    ms, (X, sts) = timed(lambda: g.pcg_solve_multi(B, max_iters=1000, tol=1e-8))
+    its = [s_.iters for s_ in sts]
+    fl = hpcg_flops_per_iter(128, 128, 128, 4) * sum(its)
+    res["multi_rhs_32x128^3"] = {"ms": ms, "iters_max": max(its), "iters_sum": sum(its),
+                                 "converged": all(s_.converged for s_ in sts), "hpcg_gflops": fl / (ms * 1e-3) / 1e9}
+    del g, B, X
+    # (b) 64 grids with edges from {32,48,64,80,96} (seed 3), 4 levels, to 1e-8
+    dims = [tuple(int(v) for v in d) for d in uneven_batch_dims(64, seed=3)]
+    bat = HpcgBatch(dims, levels=4, device=dev)
+    bb = torch.as_tensor(normal(bat.n, 3), device=dev)
+    ms, (xb, sts) = timed(lambda: bat.pcg_solve(bb, max_iters=1000, tol=1e-8))
+    fl = sum(hpcg_flops_per_iter(*d, 4) * s_.iters for d, s_ in zip(dims, sts))
+    res["batch_64_uneven_grids"] = {"ms": ms, "rows": bat.n, "iters_max": max(s_.iters for s_ in sts),
+                                    "converged": all(s_.converged for s_ in sts), "hpcg_gflops": fl / (ms * 1e-3) / 1e9}
+    del bat, bb, xb
+    # (c) differentiable solve at 96^3: forward + adjoint backward, FP64 outer, FP32 M
+    n = 96 ** 3
+    kappa, b, xt = differentiable_inputs(n, seed=4)
+    g = HpcgProblem(96, 96, 96, levels=4, precision="mixed", device=dev)
+    kt = torch.as_tensor(kappa, device=dev).requires_grad_(True)
+    bt = torch.as_tensor(b, device=dev).requires_grad_(True)
+    xtt = torch.as_tensor(xt, device=dev)
+
+    def fwd_bwd():
+        kt.grad = None
+        bt.grad = None
+        x = hpcg_solve(bt, kt, g, max_iters=1000, tol=1e-10)
+        loss = 0.5 * ((x - xtt) ** 2).sum()
+        loss.backward()
+        return loss
+
+    ms, loss = timed(fwd_bwd)
+    res["differentiable_96^3"] = {"ms_forward_backward": ms, "loss": float(loss), "tol": 1e-10}
+    return res
 
 
 def run_reference(args):
@@ -186,6 +258,8 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     n = NX * NY * NZ
     prob = HpcgProblem(NX, NY, NZ, levels=LEVELS, device=dev)
+    if args.shapes:
+        prob.set_launch_shapes(json.loads(args.shapes))
     b = prob.get_rhs()
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
@@ -235,39 +309,63 @@ def run_gpu(args):
         if rank == 0:
             print(json.dumps({"metric": "HPCG-rule GFLOP/s (quick profiling run)", "value": value, "unit": "GFLOP/s",
                               "ms_per_step": ms, "grid": [NX, NY, NZ], "gpu_launches": launches,
-                              "max_abs_err_vs_ones": err_ones}), flush=True)
+                              "max_abs_err_vs_ones": err_ones,
+                              "shapes": json.loads(args.shapes) if args.shapes else "autotuned"}), flush=True)
         return 0
 
-    # --- dominant kernel: one colour step of the smoother on the finest level,
-    # timed with CUDA events on the launching stream (torch's current stream)
+    # --- dominant kernel: the colour-pair line kernel (k_gs_lines<double>) on
+    # the finest level, timed over whole smoother applications (7 launches:
+    # runs [0,1] [2,3] [4,5] [6,7,6] [5,4] [3,2] [1,0]) with CUDA events on
+    # the launching stream (torch's current stream)
+    shapes = tuned_shapes(prob)
+    zc = shapes[0][3]
     r = torch.randn(n, dtype=torch.float64, device=dev)
     z = torch.randn(n, dtype=torch.float64, device=dev)
-    for _ in range(5):
-        prob.rbgs_color(r, z, 0)
-    reps = 64
+    for _ in range(3):
+        prob.rbgs(r, z, 0)
+    reps = 20
     torch.cuda.synchronize()
     k0 = torch.cuda.Event(enable_timing=True)
     k1 = torch.cuda.Event(enable_timing=True)
     k0.record(stream)
-    for k in range(reps):
-        prob.rbgs_color(r, z, k % 8)
+    for _ in range(reps):
+        prob.rbgs(r, z, 0)
     k1.record(stream)
     torch.cuda.synchronize()
-    k_ms = k0.elapsed_time(k1) / reps
-    upd = n // 8
-    fp64_ops_per_row = 27  # 26 neighbour/right-hand-side additions + 1 multiply by 1/A_ii
-    ops = upd * fp64_ops_per_row
-    achieved = ops / (k_ms * 1e-3) / 1e9
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    sweep_ms = k0.elapsed_time(k1) / reps
+    launches_per_sweep = 7
+    k_ms = sweep_ms / launches_per_sweep
+    # FP64 instructions per x on the updated lines of one run: plane sums 2 (+2/zc
+    # at a z-chunk start) + 1 (the two lines beside) + 2 (column sum) + 2 (x window)
+    # + 4 per colour step (3 additions, 1 multiply by 1/A_ii)
+    ops_sweep = (n // 4) * (6 * (7 + 2.0 / zc + 2 * 2) + (7 + 2.0 / zc + 2 * 3))
+    achieved = ops_sweep / (sweep_ms * 1e-3) / 1e9
     peak_nominal = 152 * 2 * 2070e6 / 1e9  # FP64 instructions per second (2 per SM per clock)
-    roofline = {"bound": "alu", "kernel": "k_gs_color<double> (finest level, one colour)", "achieved": achieved,
-                "peak": peak_nominal, "unit": "G FP64 instr/s", "frac": achieved / peak_nominal,
-                "peak_basis": "152 SMs x 2 FP64 ops/clk x 2070 MHz (nominal 1.25 TFLOP/s FMA); "
-                              "probe-measured 505 G/s at load clocks",
-                "ms_per_launch": k_ms, "fp64_ops_per_updated_row": fp64_ops_per_row,
-                "hbm_bytes_algorithmic": upd * 8 * 2 + n * 8,
-                "hbm_gbs_at_that_time": (upd * 16 + n * 8) / (k_ms * 1e-3) / 1e9, "traffic": None,
-                "sm_mhz_during_bench": sm_mhz}
+    bytes_launch = 12 * n  # z of every line read once, r and z of the class lines read/written
+    roofline = {"bound": "alu", "kernel": "k_gs_lines<double> (finest level, colour-pair runs of a symmetric sweep)",
+                "achieved": achieved, "peak": peak_nominal, "unit": "G FP64 instr/s", "frac": achieved / peak_nominal,
+                "peak_basis": "152 SMs x 2 FP64 instructions/clk x 2070 MHz (nominal 1.25 TFLOP/s FMA rate)",
+                "ms_per_launch": k_ms, "ms_per_sweep": sweep_ms, "launches_per_sweep": launches_per_sweep,
+                "fp64_instr_per_sweep": ops_sweep, "hbm_bytes_algorithmic_per_launch": bytes_launch,
+                "hbm_gbs_equivalent": bytes_launch / (k_ms * 1e-3) / 1e9, "traffic": None,
+                "launch_shapes_per_level": shapes}
+    # SpMV line kernel (secondary): 7 + 4/zc FP64 instructions per row
+    zr = shapes[0][1]
+    xs_ = torch.randn(n, dtype=torch.float64, device=dev)
+    ys_ = torch.empty_like(xs_)
+    for _ in range(3):
+        prob.spmv(xs_, out=ys_)
+    torch.cuda.synchronize()
+    k0.record(stream)
+    for _ in range(reps):
+        prob.spmv(xs_, out=ys_)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    sp_ms = k0.elapsed_time(k1) / reps
+    spmv = {"kernel": "k_spmv_lines<double>", "ms": sp_ms, "fp64_instr_per_row": 7 + 4.0 / zr,
+            "g_fp64_instr_s": n * (7 + 4.0 / zr) / (sp_ms * 1e-3) / 1e9,
+            "hbm_gbs_algorithmic": 16 * n / (sp_ms * 1e-3) / 1e9}
+    del xs_, ys_
 
     # --- mixed vs FP64 time to 1e-9 (b = A x_true, x_true ~ U[-1,1], seed 1)
     xt = torch.as_tensor(mixed_precision_xtrue(n, seed=1), device=dev)
@@ -291,6 +389,8 @@ def run_gpu(args):
     mixed_vs["speedup"] = res["fp64"]["ms"] / res["mixed"]["ms"]
     mixed_vs["mixed_vs_fp64_x"] = float((res["mixed"]["x"] - res["fp64"]["x"]).abs().max() / res["fp64"]["x"].abs().max())
     del res
+
+    forms = {} if args.skip_forms else other_forms(dev, stream)
 
     # --- end to end through the public API with host buffers
     b_h = b.cpu().pin_memory()
@@ -345,6 +445,8 @@ def run_gpu(args):
         "roofline": roofline,
         "hbm_peak": {"value": peaks.get("hbm_gbs"), "kind": kind},
         "mixed_vs_fp64_to_1e-9": mixed_vs,
+        "spmv": spmv,
+        "forms": forms,
         "e2e": e2e,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -361,6 +463,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=192, help="cubic grid edge (profiling runs; default 192)")
+    ap.add_argument("--skip-forms", action="store_true", help="skip the batched and differentiable form timings")
+    ap.add_argument("--shapes", default=None,
+                    help="JSON list of per-level launch shapes [[row lines, row planes, line lines, line planes], ...] "
+                         "to use instead of autotuning (repeatable profiling runs)")
     ap.add_argument("--quick", action="store_true",
                     help="time the FP64 solve only (no kernel roofline, mixed comparison, e2e or CPU baseline)")
     args = ap.parse_args()

@@ -66,6 +66,8 @@ typedef struct {
                        this many iterations (default 1; work after convergence is skipped
                        on the device, so a larger value only costs idle launches) */
   int max_rhs;      /* largest nrhs of hpcg_pcg_solve_multi the workspace is sized for (default 0) */
+  int autotune;     /* 1 (default): the first compute call times candidate launch shapes of the
+                       line kernels on every level and keeps the fastest (hpcg_autotune) */
 } hpcg_options;
 
 typedef struct {
@@ -193,6 +195,23 @@ int hpcg_batch_offsets(hpcg_handle h, long *offsets_host);
  * (nullable) is an array of `count` records.  Each instance stops on its own. */
 int hpcg_pcg_solve_batch(hpcg_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol,
                          hpcg_stats *stats, void *stream);
+
+/* --- launch-shape autotuner ------------------------------------------------------------ */
+/* Times candidate launch shapes (x-lines per block, z-planes per block) of the
+ * SpMV and colour-step line kernels on every level of the handle and keeps the
+ * fastest; results stay bit-identical whatever the shape.  Synchronises
+ * `stream`; must not be called while `stream` is being captured.  Runs once on
+ * the first compute call when hpcg_options.autotune is set.  shapes_host
+ * (nullable) receives 4 ints per level: row lines, row planes, colour-line
+ * lines, colour-line planes. */
+int hpcg_autotune(hpcg_handle h, int *shapes_host, void *stream);
+
+/* Sets the launch shapes (same 4 ints per level as hpcg_autotune reports, each
+ * lines-per-block in 1..8 and planes-per-block in 1..64) instead of tuning, so
+ * that a run can be repeated with the same launches (profiling).  Marks the
+ * handle as tuned.  Errors: INVALID_ARG for a null pointer or a value out of
+ * range. */
+int hpcg_set_launch_shapes(hpcg_handle h, const int *shapes_host);
 
 /* --- allocation-free V-cycle ---------------------------------------------------------- */
 /* No counterpart in the paper: a convenience for callers that cannot allocate

@@ -16,7 +16,7 @@ _d = ctypes.c_double
 
 class hpcg_options(ctypes.Structure):
     _fields_ = [("nx", _i), ("ny", _i), ("nz", _i), ("levels", _i), ("precision", _i), ("pre_sweeps", _i),
-                ("post_sweeps", _i), ("symmetric", _i), ("check_every", _i), ("max_rhs", _i)]
+                ("post_sweeps", _i), ("symmetric", _i), ("check_every", _i), ("max_rhs", _i), ("autotune", _i)]
 
 
 class hpcg_stats(ctypes.Structure):
@@ -53,6 +53,8 @@ SIGNATURES = {
     "hpcg_batch_offsets": (_i, [_vp, ctypes.POINTER(_l)]),
     "hpcg_pcg_solve_batch": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
     "hpcg_mg_vcycle_noalloc": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
+    "hpcg_autotune": (_i, [_vp, ctypes.POINTER(_i), _vp]),
+    "hpcg_set_launch_shapes": (_i, [_vp, ctypes.POINTER(_i)]),
     "hpcg_strerror": (ctypes.c_char_p, [_i]),
     "hpcg_last_cuda_error": (ctypes.c_char_p, []),
     "hpcg_launch_count": (_l, []),

@@ -107,6 +107,17 @@ class HpcgProblem:
         a, b, c = self.level_dims(level)
         return a * b * c
 
+    def autotune(self):
+        """Re-times the line-kernel launch shapes; returns them per level."""
+        buf = (ctypes.c_int * (4 * self.levels))()
+        check(self.lib.hpcg_autotune(self.h, buf, _stream()), "hpcg_autotune")
+        return [list(buf[4 * l:4 * l + 4]) for l in range(self.levels)]
+
+    def set_launch_shapes(self, shapes):
+        flat = [int(v) for lv in shapes for v in lv]
+        buf = (ctypes.c_int * len(flat))(*flat)
+        check(self.lib.hpcg_set_launch_shapes(self.h, buf), "hpcg_set_launch_shapes")
+
     def set_kappa(self, kappa):
         if kappa is not None:
             kappa = _need(kappa, self.n, name="kappa")

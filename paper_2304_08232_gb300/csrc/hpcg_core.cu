@@ -53,8 +53,10 @@ static int nch_supported(int need) {
 }
 
 static void set_line_prefixes(LevelData &L) {
-  int br = 0, bl = 0;
+  int br = 0, bl = 0, po = 0;
   for (Inst &g : L.inst) {
+    g.poff = po;
+    po += g.ny * g.nz;
     g.blk_row = br;
     g.nrow = row_blocks(g.ny, g.nz, L.tab.row_lpc, L.tab.row_zc);
     g.blk_line = bl;
@@ -73,6 +75,18 @@ static void choose_line_params(LevelData &L) {
   int nxm = 0;
   for (const Inst &g : L.inst) nxm = std::max(nxm, g.nx);
   L.tab.nch = nch_supported((nxm + 31) / 32);
+  // colour-step kernels hold each line split by x parity: ceil(nx/2) per parity
+  {
+    const int need = (((nxm + 1) / 2) + 31) / 32;
+    static const int avail2[] = {1, 2, 3, 4, 5, 6, 8};
+    L.tab.nch2 = 0;
+    for (int a : avail2)
+      if (a >= need) {
+        L.tab.nch2 = a;
+        break;
+      }
+    if (L.tab.nch2 == 0) L.tab.nch = 0;  // lines too long for the registers: one-thread-per-row kernels
+  }
   const int target = 2 * 152;
   auto pick = [&](bool lines_of_class, int *lpc_out, int *zc_out) {
     static const int lpcs[] = {8, 4, 2, 1};
@@ -128,7 +142,7 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
       g.blk_half = bh;
       g.blk_red = br;
       g.nred = red_blocks(g.n);
-      g.pad = 0;
+      g.poff = 0;
       rows += g.n;
       bf += tiles_of(g.nx, g.ny, g.nz);
       bh += tiles_of(half_up(g.nx), half_up(g.ny), half_up(g.nz));
@@ -146,7 +160,10 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
   h->o_st = take(sizeof(CgState) * h->count);
   h->o_hist = take(sizeof(double) * (size_t)kHistoryCap * h->count);
   const LevelData &L0 = h->lv[0];
-  h->npart = (size_t)std::max(std::max(std::max(L0.tab.nblk_full, L0.tab.nblk_red), L0.tab.nblk_row), kRawDotBlocks) + 64;
+  // partial sums: enough for any launch shape the autotuner may pick (one line per block at most)
+  long max_row_blocks = 0;
+  for (const Inst &g : L0.inst) max_row_blocks += (long)g.ny * g.nz;
+  h->npart = (size_t)std::max(std::max((long)std::max(L0.tab.nblk_full, L0.tab.nblk_red), max_row_blocks), (long)kRawDotBlocks) + 64;
   h->o_part = take(sizeof(double) * h->npart);
   h->o_out = take(sizeof(double) * (h->count + 64));
   const long n0 = L0.n;
@@ -229,6 +246,7 @@ static int bind(hpcg_ctx *h, char *ws, size_t bytes, bool owned) {
 }
 
 static int set_kappa_impl(hpcg_ctx *h, const double *kappa, cudaStream_t s);
+static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s);
 
 int ensure_ready(hpcg_ctx *h, cudaStream_t s) {
   if (!h->ready) {
@@ -244,6 +262,10 @@ int ensure_ready(hpcg_ctx *h, cudaStream_t s) {
     const double *k = h->kappa_pending;
     h->kappa_pending = nullptr;
     TRY(set_kappa_impl(h, k, s));
+  }
+  if (h->opt.autotune && !h->tuned) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) TRY(autotune_impl(h, nullptr, s));
   }
   return HPCG_OK;
 }
@@ -309,27 +331,42 @@ const double *invd_of<double>(const LevelData &L, bool has) { return has ? L.inv
 template <>
 const float *invd_of<float>(const LevelData &L, bool has) { return has ? L.invd32 : nullptr; }
 
-template <typename T, int NCH>
-static void launch_gs_lines(const LevelData &L, int count, int py, int pz, int pa, int steps, const T *r, T *z, const T *invd,
-                            const CgState *st, cudaStream_t s) {
-  k_gs_lines<T, NCH><<<L.tab.nblk_line, dim3(32, L.tab.line_lpc), 0, s>>>(L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa,
-                                                                         steps, r, z, invd, st);
+template <typename T>
+static int enqueue_zero(hpcg_ctx *h, int l, T *v, cudaStream_t s, const CgState *st) {
+  const LevelData &L = h->lv[l];
+  k_zero_inst<T><<<L.tab.nblk_red, kRedThreads, 0, s>>>(L.tab.inst, h->count, v, st);
+  CKL("k_zero_inst");
+  return HPCG_OK;
 }
 
-// `steps` colour steps on the lines of class (py, pz), alternating x parity from pa.
+template <typename T, int NCH>
+static void launch_gs_lines(const LevelData &L, int count, int py, int pz, int pa, int steps, int vmask, const T *r, T *z, const T *invd,
+                            const CgState *st, const Inst *tabc, T *rc, const T *kap, cudaStream_t s) {
+  k_gs_lines<T, NCH><<<L.tab.nblk_line, dim3(32, L.tab.line_lpc), 0, s>>>(L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa,
+                                                                         steps, vmask, r, z, invd, st, tabc, rc, kap);
+}
+
+// `steps` colour steps on the lines of class (py, pz), alternating x parity
+// from pa.  vmask: line classes holding valid z (others count as zero).  rc
+// (nullable, class (0,0) runs ending on even x): fused residual + injection
+// into level l+1.
 template <typename T>
 static int enqueue_line_steps(hpcg_ctx *h, int l, int py, int pz, int pa, int steps, const T *r, T *z, cudaStream_t s,
-                              const CgState *st) {
+                              const CgState *st, int vmask = 0xF, T *rc = nullptr) {
   const LevelData &L = h->lv[l];
   const T *invd = invd_of<T>(L, h->has_kappa);
-  switch (L.tab.nch) {
+  const T *kap = kap_of<T>(L, h->has_kappa);
+  const Inst *tabc = rc ? h->lv[l + 1].tab.inst : nullptr;
+  switch (L.tab.nch ? L.tab.nch2 : 0) {
 #define HPCG_GS_CASE(N) \
-  case N: launch_gs_lines<T, N>(L, h->count, py, pz, pa, steps, r, z, invd, st, s); break;
+  case N: launch_gs_lines<T, N>(L, h->count, py, pz, pa, steps, vmask, r, z, invd, st, tabc, rc, kap, s); break;
     HPCG_GS_CASE(1) HPCG_GS_CASE(2) HPCG_GS_CASE(3) HPCG_GS_CASE(4) HPCG_GS_CASE(5) HPCG_GS_CASE(6)
-    HPCG_GS_CASE(7) HPCG_GS_CASE(8) HPCG_GS_CASE(10) HPCG_GS_CASE(12) HPCG_GS_CASE(16)
+    HPCG_GS_CASE(8)
 #undef HPCG_GS_CASE
     default: {
       // lines longer than the register window: one launch per colour step
+      // (callers zero z first and restrict separately on this path)
+      if (rc || vmask != 0xF) return HPCG_ERR_UNSUPPORTED;
       for (int k = 0; k < steps; ++k) {
         const int px = (k & 1) ? 1 - pa : pa;
         k_gs_color<T><<<L.tab.nblk_half, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, px, py, pz, r, z, invd, st);
@@ -349,15 +386,33 @@ static int enqueue_colour(hpcg_ctx *h, int l, int k, const T *r, T *z, cudaStrea
 
 // The smoother's colour sequence grouped into runs of one line class: the
 // colours 2m, 2m+1 of a run share (y, z) parities and alternate in x parity.
+// from_zero: z holds no valid values yet (it counts as zero; nothing needs to
+// be cleared first).  rc (nullable): restrict the residual into it, fused into
+// the last run when that run is class (0,0) ending on even x; *fused tells
+// whether that happened.
 template <typename T>
-static int enqueue_smoother(hpcg_ctx *h, int l, const T *r, T *z, int sweeps, cudaStream_t s, const CgState *st) {
+static int enqueue_smoother(hpcg_ctx *h, int l, const T *r, T *z, int sweeps, cudaStream_t s, const CgState *st,
+                            bool from_zero = false, T *rc = nullptr, bool *fused = nullptr) {
   const std::vector<int> seq = phase_sequence(sweeps, h->opt.symmetric);
+  const bool lines = h->lv[l].tab.nch > 0;
+  if (fused) *fused = false;
+  if (from_zero && !lines) TRY(enqueue_zero<T>(h, l, z, s, st));
+  int vmask = (from_zero && lines) ? 0 : 0xF;
   size_t i = 0;
   while (i < seq.size()) {
     size_t j = i + 1;
     while (j < seq.size() && (seq[j] >> 1) == (seq[i] >> 1)) ++j;
     const int k = seq[i];
-    TRY(enqueue_line_steps<T>(h, l, (k >> 1) & 1, (k >> 2) & 1, k & 1, (int)(j - i), r, z, s, st));
+    const int steps = (int)(j - i);
+    const int cls = k >> 1;
+    const int last_parity = (steps & 1) ? (k & 1) : 1 - (k & 1);
+    T *rc_here = nullptr;
+    if (rc && lines && j == seq.size() && cls == 0 && last_parity == 0) {
+      rc_here = rc;
+      if (fused) *fused = true;
+    }
+    TRY(enqueue_line_steps<T>(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, z, s, st, vmask, rc_here));
+    vmask |= 1 << cls;
     i = j;
   }
   return HPCG_OK;
@@ -404,23 +459,20 @@ static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s
   return HPCG_OK;
 }
 
-template <typename T>
-static int enqueue_zero(hpcg_ctx *h, int l, T *v, cudaStream_t s, const CgState *st) {
-  const LevelData &L = h->lv[l];
-  k_zero_inst<T><<<L.tab.nblk_red, kRedThreads, 0, s>>>(L.tab.inst, h->count, v, st);
-  CKL("k_zero_inst");
-  return HPCG_OK;
-}
 
 // Listing 1 on levels 0..L-1; rl[l], zl[l] are the level vectors in precision T.
 template <typename T>
 static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_t s, const CgState *st) {
   const int L = h->levels;
   for (int l = 0; l < L; ++l) {
-    TRY(enqueue_zero<T>(h, l, zl[l], s, st));                                   // z <- 0
-    TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], l == L - 1 ? 1 : h->opt.pre_sweeps, s, st));  // pre-smoothing
-    if (l == L - 1) break;                                                      // coarsest: return
-    TRY(enqueue_restrict<T>(h, l, rl[l], zl[l], rl[l + 1], s, st));             // r_c <- restrict(r - A z)
+    // z <- 0 and pre-smoothing; on the way down the residual restriction
+    // r_c <- restrict(r - A z) is fused into the smoother's last run when it
+    // can be, else it is its own launch
+    bool fused = false;
+    TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], l == L - 1 ? 1 : h->opt.pre_sweeps, s, st, true,
+                            l == L - 1 ? nullptr : rl[l + 1], &fused));
+    if (l == L - 1) break;  // coarsest: return
+    if (!fused) TRY(enqueue_restrict<T>(h, l, rl[l], zl[l], rl[l + 1], s, st));
   }
   for (int l = L - 2; l >= 0; --l) {
     TRY(enqueue_prolong<T>(h, l, zl[l + 1], zl[l], s, st));                     // z <- z + refine(z_c)
@@ -623,8 +675,141 @@ static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, doubl
 }
 
 // ---------------------------------------------------------------------------
+// Launch-shape autotuner: for every level, times each candidate (lines per
+// block, planes per block) of the SpMV line kernel and of the colour-pair line
+// kernel on the level's own vectors and keeps the fastest.  The shape changes
+// only how lines are grouped into blocks, never the arithmetic of a row.
+static int time_shape(hpcg_ctx *h, int l, bool rows, int lpc, int zc, cudaStream_t s, float *ms) {
+  LevelData &L = h->lv[l];
+  if (rows) {
+    L.tab.row_lpc = lpc;
+    L.tab.row_zc = zc;
+  } else {
+    L.tab.line_lpc = lpc;
+    L.tab.line_zc = zc;
+  }
+  set_line_prefixes(L);
+  CK(cudaMemcpyAsync((void *)L.tab.inst, L.inst.data(), sizeof(Inst) * h->count, cudaMemcpyHostToDevice, s));
+  double *a = l == 0 ? h->cg_r : L.r;
+  double *b = l == 0 ? h->cg_z : L.z;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = HPCG_OK;
+  const int reps = 3;
+  for (int it = 0; it <= reps && rc == HPCG_OK; ++it) {
+    if (it == 1) cudaEventRecord(e0, s);
+    if (rows)
+      rc = enqueue_spmv<double, 0>(h, l, a, nullptr, b, nullptr, nullptr, nullptr, s);
+    else
+      rc = enqueue_line_steps<double>(h, l, 0, 0, 0, 2, a, b, s, nullptr);
+  }
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HPCG_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+  *ms = t / reps;
+  return HPCG_OK;
+}
+
+static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s) {
+  static const int lpcs[] = {1, 2, 4, 8};
+  static const int zcs[] = {1, 2, 4, 8, 16};
+  for (int l = 0; l < h->levels; ++l) {
+    LevelData &L = h->lv[l];
+    if (L.tab.nch == 0) continue;
+    double *a = l == 0 ? h->cg_r : L.r;
+    double *b = l == 0 ? h->cg_z : L.z;
+    CK(cudaMemsetAsync(a, 0, sizeof(double) * L.n, s));
+    CK(cudaMemsetAsync(b, 0, sizeof(double) * L.n, s));
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool rows = pass == 0;
+      float best = 1e30f;
+      int bl = rows ? L.tab.row_lpc : L.tab.line_lpc, bz = rows ? L.tab.row_zc : L.tab.line_zc;
+      for (int zc : zcs)
+        for (int lpc : lpcs) {
+          float ms = 0.f;
+          TRY(time_shape(h, l, rows, lpc, zc, s, &ms));
+          if (ms < best) {
+            best = ms;
+            bl = lpc;
+            bz = zc;
+          }
+        }
+      if (rows) {
+        L.tab.row_lpc = bl;
+        L.tab.row_zc = bz;
+      } else {
+        L.tab.line_lpc = bl;
+        L.tab.line_zc = bz;
+      }
+      set_line_prefixes(L);
+    }
+    CK(cudaMemcpyAsync((void *)L.tab.inst, L.inst.data(), sizeof(Inst) * h->count, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  // partial-sum buffers are sized by the largest launch: keep within them
+  const size_t need_part = (size_t)std::max(std::max(h->lv[0].tab.nblk_full, h->lv[0].tab.nblk_red), h->lv[0].tab.nblk_row) + 64;
+  if (need_part > h->npart) return HPCG_ERR_NO_WORKSPACE;
+  if (shapes)
+    for (int l = 0; l < h->levels; ++l) {
+      shapes[4 * l + 0] = h->lv[l].tab.row_lpc;
+      shapes[4 * l + 1] = h->lv[l].tab.row_zc;
+      shapes[4 * l + 2] = h->lv[l].tab.line_lpc;
+      shapes[4 * l + 3] = h->lv[l].tab.line_zc;
+    }
+  if (h->g_iter.exec) {  // captured with the previous block counts
+    cudaGraphExecDestroy(h->g_iter.exec);
+    h->g_iter = GraphCache{};
+  }
+  h->tuned = true;
+  return HPCG_OK;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 extern "C" {
+
+int hpcg_set_launch_shapes(hpcg_handle h, const int *shapes_host) {
+  if (!h || !shapes_host) return HPCG_ERR_INVALID_ARG;
+  for (int l = 0; l < h->levels; ++l)
+    for (int k = 0; k < 4; ++k) {
+      const int v = shapes_host[4 * l + k];
+      if (v < 1 || v > ((k & 1) ? 64 : 8)) return HPCG_ERR_INVALID_ARG;
+    }
+  std::lock_guard<std::mutex> lk(h->mu);
+  for (int l = 0; l < h->levels; ++l) {
+    LevelData &L = h->lv[l];
+    L.tab.row_lpc = shapes_host[4 * l + 0];
+    L.tab.row_zc = shapes_host[4 * l + 1];
+    L.tab.line_lpc = shapes_host[4 * l + 2];
+    L.tab.line_zc = shapes_host[4 * l + 3];
+    set_line_prefixes(L);
+    if (h->ready) CK(cudaMemcpy((void *)L.tab.inst, L.inst.data(), sizeof(Inst) * h->count, cudaMemcpyHostToDevice));
+  }
+  if (h->g_iter.exec) {
+    cudaGraphExecDestroy(h->g_iter.exec);
+    h->g_iter = GraphCache{};
+  }
+  h->tuned = true;
+  return HPCG_OK;
+}
+
+int hpcg_autotune(hpcg_handle h, int *shapes_host, void *stream) {
+  if (!h) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int tune = h->opt.autotune;
+  h->opt.autotune = 0;  // ensure_ready must not tune on its own here
+  int rc = ensure_ready(h, s);
+  h->opt.autotune = tune;
+  if (rc != HPCG_OK) return rc;
+  return autotune_impl(h, shapes_host, s);
+}
 
 int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   if (!opt) return HPCG_ERR_INVALID_ARG;
@@ -639,6 +824,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->symmetric = 1;
   opt->check_every = 1;
   opt->max_rhs = 0;
+  opt->autotune = 1;
   return HPCG_OK;
 }
 
@@ -953,7 +1139,7 @@ __global__ void k_noalloc_tables(int nx, int ny, int nz, int levels, Inst *__res
     g.blk_row = g.nrow = g.blk_line = g.nline = 0;
     long b = (g.n + (long)kRedThreads * kRedItems - 1) / ((long)kRedThreads * kRedItems);
     g.nred = (int)(b < 1 ? 1 : (b > kMaxRedBlocksPerInst ? kMaxRedBlocksPerInst : b));
-    g.pad = 0;
+    g.poff = 0;
     tabs[l] = g;
   }
 }

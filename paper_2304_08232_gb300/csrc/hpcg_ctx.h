@@ -79,6 +79,7 @@ struct hpcg_ctx {
   cudaStream_t cap = nullptr;
   GraphCache g_iter;
   GraphCache g_multi;
+  bool tuned = false;
   int device = 0;
   std::mutex mu;
 };

@@ -61,11 +61,23 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return s;
 }
 
-// Fixed-order sum of partials[first .. first+cnt) inside one block; valid in thread 0.
+// Fixed-order sum of partials[first .. first+cnt) inside one block; valid in
+// thread 0.  Thread t sums elements t + k*blockDim in four interleaved
+// accumulators (independent load/add chains), combined in a fixed order.
 __device__ __forceinline__ double sum_partials(const double *__restrict__ partials, int first, int cnt, double *sh) {
-  double s = 0.0;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) s += partials[first + k];
-  return block_sum(s, sh);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const int bd = blockDim.x;
+  int k = threadIdx.x;
+  for (; k + 3 * bd < cnt; k += 4 * bd) {
+    a0 += partials[first + k];
+    a1 += partials[first + k + bd];
+    a2 += partials[first + k + 2 * bd];
+    a3 += partials[first + k + 3 * bd];
+  }
+  if (k < cnt) a0 += partials[first + k];
+  if (k + bd < cnt) a1 += partials[first + k + bd];
+  if (k + 2 * bd < cnt) a2 += partials[first + k + 2 * bd];
+  return block_sum((a0 + a1) + (a2 + a3), sh);
 }
 
 enum FinKind { FIN_NORM0 = 0, FIN_RTZ = 1, FIN_PAP = 2, FIN_NORM = 3, FIN_OUT = 4 };

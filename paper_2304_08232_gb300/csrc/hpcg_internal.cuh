@@ -35,7 +35,7 @@ struct Inst {
   int nrow;       // blocks of this grid in that launch
   int blk_line;   // first block in a line launch over the lines of one colour-line class
   int nline;      // blocks of this grid in that launch
-  int pad;
+  int poff;       // first per-line partial sum of this grid (prefix of ny * nz)
   long off;       // first row of this grid in the level's concatenated vectors
   long n;         // rows
 };
@@ -48,6 +48,7 @@ struct LevelTab {
   int row_lpc, row_zc;    // line launch over all lines: lines (warps) per block, z-planes per block
   int line_lpc, line_zc;  // line launch over one line class: lines per block, updated planes per block
   int nch;                // 32-wide x chunks per line (ceil(max nx / 32)); 0 = line kernels unavailable
+  int nch2;               // 32-wide chunks per x parity (ceil(ceil(max nx / 2) / 32)) of the colour-step kernels
   long n;                 // rows over all instances
 };
 

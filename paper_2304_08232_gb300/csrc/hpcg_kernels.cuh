@@ -222,9 +222,9 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const Inst *__restrict
   const int ii = blockIdx.x;
   const Inst g = tab[ii];
   int first, cnt;
-  if (stencil == 2) {  // line SpMV blocking
-    first = g.blk_row;
-    cnt = g.nrow;
+  if (stencil == 2) {  // line SpMV: one partial per x-line
+    first = g.poff;
+    cnt = g.ny * g.nz;
   } else if (stencil == 1) {  // 32x8 tile blocking
     first = g.blk_full;
     cnt = tiles_of(g.nx, g.ny, g.nz);

@@ -39,22 +39,30 @@ __device__ __forceinline__ void line_neighbours(const T (&v)[NCH], T (&vl)[NCH],
   }
 }
 
+// Line class of line (y, z): its y and z parities, (y & 1) + 2 (z & 1).
+__device__ __forceinline__ int line_class(int y, int z) { return (y & 1) + 2 * (z & 1); }
+
 // Sum over y-1, y, y+1 of line (., y, zz) of the grid at zg (zero outside).
+// Lines whose class bit is clear in vmask hold no valid data yet and count as
+// zero (smoothing from z = 0 without clearing z first).
 template <typename T, int NCH>
-__device__ __forceinline__ void tsum(const T *__restrict__ zg, int nx, int ny, int nz, int y, int zz, int lane, T (&t)[NCH]) {
+__device__ __forceinline__ void tsum(const T *__restrict__ zg, int nx, int ny, int nz, int y, int zz, int lane, T (&t)[NCH],
+                                     int vmask = 0xF) {
   const bool zin = zz >= 0 && zz < nz;
   const long sxy = (long)nx * ny;
   const T *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
   const T *l0 = lm + nx;
   const T *lp = l0 + nx;
-  const bool ym = y - 1 >= 0, yp = y + 1 < ny;
+  const bool ym = y - 1 >= 0 && ((vmask >> line_class(y + 1, zz)) & 1);  // y-1 and y+1 share a class
+  const bool yp = y + 1 < ny && ((vmask >> line_class(y + 1, zz)) & 1);
+  const bool y0 = (vmask >> line_class(y, zz)) & 1;
 #pragma unroll
   for (int c = 0; c < NCH; ++c) {
     const int x = lane + 32 * c;
     T s = T(0);
     if (zin && x < nx) {
       const T a = ym ? __ldg(lm + x) : T(0);
-      const T b = __ldg(l0 + x);
+      const T b = y0 ? __ldg(l0 + x) : T(0);
       const T d = yp ? __ldg(lp + x) : T(0);
       s = (a + b) + d;
     }
@@ -62,13 +70,67 @@ __device__ __forceinline__ void tsum(const T *__restrict__ zg, int nx, int ny, i
   }
 }
 
+// Parity-split registers of a line: lane l holds E[c] = v(x = 2k) and
+// O[c] = v(x = 2k + 1) for k = l + 32c, so that a colour step (one x parity)
+// keeps all 32 lanes busy.  Neighbours along x: for even x = 2k they are
+// O[k-1] and O[k]; for odd x = 2k+1 they are E[k] and E[k+1].
+template <typename T, int NC>
+__device__ __forceinline__ void prev_of(const T (&v)[NC], T (&out)[NC], int lane) {  // out[k] = v[k-1]
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const T up = __shfl_up_sync(kFull, v[c], 1);
+    const T last = __shfl_sync(kFull, v[c > 0 ? c - 1 : 0], 31);
+    out[c] = lane == 0 ? (c > 0 ? last : T(0)) : up;
+  }
+}
+template <typename T, int NC>
+__device__ __forceinline__ void next_of(const T (&v)[NC], T (&out)[NC], int lane) {  // out[k] = v[k+1]
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const T dn = __shfl_down_sync(kFull, v[c], 1);
+    const T first = __shfl_sync(kFull, v[c + 1 < NC ? c + 1 : c], 0);
+    out[c] = lane == 31 ? (c + 1 < NC ? first : T(0)) : dn;
+  }
+}
+
+// Sum over y-1, y, y+1 of line (., y, zz) at even (te) and odd (to) x.
+template <typename T, int NC>
+__device__ __forceinline__ void tsum2(const T *__restrict__ zg, int nx, int ny, int nz, int y, int zz, int lane, T (&te)[NC],
+                                      T (&to)[NC], int vmask) {
+  const bool zin = zz >= 0 && zz < nz;
+  const long sxy = (long)nx * ny;
+  const T *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
+  const T *l0 = lm + nx;
+  const T *lp = l0 + nx;
+  const bool ym = zin && y - 1 >= 0 && ((vmask >> line_class(y + 1, zz)) & 1);
+  const bool yp = zin && y + 1 < ny && ((vmask >> line_class(y + 1, zz)) & 1);
+  const bool y0 = zin && ((vmask >> line_class(y, zz)) & 1);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+    T se = T(0), so = T(0);
+    if (xe < nx) se = ((ym ? __ldg(lm + xe) : T(0)) + (y0 ? __ldg(l0 + xe) : T(0))) + (yp ? __ldg(lp + xe) : T(0));
+    if (xo < nx) so = ((ym ? __ldg(lm + xo) : T(0)) + (y0 ? __ldg(l0 + xo) : T(0))) + (yp ? __ldg(lp + xo) : T(0));
+    te[c] = se;
+    to[c] = so;
+  }
+}
+
 // Colour steps on the lines of class (py, pz): `steps` alternating x parities
 // starting with `pa`.  Block = 32 x lpc threads (lpc lines), zc updated planes
 // per block.  Reads z of the 3x3 line neighbourhood, writes z on its own lines.
-template <typename T, int NCH>
+//
+// vmask: line classes whose z values are valid; the others count as zero (the
+// first forward sweep from z = 0).  rc (nullable): fused residual + injection
+// (Listing 1 lines 5-6) after the last step, for a run on class (0, 0) that
+// ends on even x: every injected fine row (2xc, 2yc, 2zc) lies on these lines,
+// its neighbour sum is P + z(x-1) + z(x+1) with values final for this
+// smoother application, so rc[c] = r - (A_ii z - that sum) is formed here.
+template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
-                                                  int steps, const T *__restrict__ r, T *__restrict__ z, const T *__restrict__ invd,
-                                                  const CgState *__restrict__ st) {
+                                                  int steps, int vmask, const T *__restrict__ r, T *__restrict__ z,
+                                                  const T *__restrict__ invd, const CgState *__restrict__ st, const Inst *__restrict__ tabc,
+                                                  T *__restrict__ rc, const T *__restrict__ kap) {
   const int blk = blockIdx.x;
   const int ii = find_inst<4>(tab, count, blk);
   const Inst g = tab[ii];
@@ -86,67 +148,108 @@ __global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, 
   const long sxy = (long)nx * g.ny;
   T *zg = z + g.off;
   const T *rg = r + g.off;
-  const bool ym = y - 1 >= 0, yp = y + 1 < g.ny;
-  T tprev[NCH];
-  tsum<T, NCH>(zg, nx, g.ny, g.nz, y, 2 * m0 + pz - 1, lane, tprev);
+  const int cls_v = line_class(y + 1, pz);  // lines (y +- 1, zz)
+  const bool ym = y - 1 >= 0 && ((vmask >> cls_v) & 1), yp = y + 1 < g.ny && ((vmask >> cls_v) & 1);
+  const bool own_valid = (vmask >> line_class(y, pz)) & 1;
+  T tpe[NC], tpo[NC];
+  tsum2<T, NC>(zg, nx, g.ny, g.nz, y, 2 * m0 + pz - 1, lane, tpe, tpo, vmask);
   for (int m = m0; m < m1; ++m) {
     const int zz = 2 * m + pz;
-    T tnext[NCH], P[NCH];
-    tsum<T, NCH>(zg, nx, g.ny, g.nz, y, zz + 1, lane, tnext);
+    T tne[NC], tno[NC], PE[NC], PO[NC];
+    tsum2<T, NC>(zg, nx, g.ny, g.nz, y, zz + 1, lane, tne, tno, vmask);
     {
-      T cc[NCH], cl[NCH], cr[NCH];
+      T ce[NC], co[NC], sh[NC];
       const T *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
       const T *lp = lm + 2 * nx;
 #pragma unroll
-      for (int c = 0; c < NCH; ++c) {
-        const int x = lane + 32 * c;
-        T v = T(0);
-        if (x < nx) v = (ym ? __ldg(lm + x) : T(0)) + (yp ? __ldg(lp + x) : T(0));
-        cc[c] = (tprev[c] + tnext[c]) + v;  // off-line column sum at x
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+        T ve = T(0), vo = T(0);
+        if (xe < nx) ve = (ym ? __ldg(lm + xe) : T(0)) + (yp ? __ldg(lp + xe) : T(0));
+        if (xo < nx) vo = (ym ? __ldg(lm + xo) : T(0)) + (yp ? __ldg(lp + xo) : T(0));
+        ce[c] = (tpe[c] + tne[c]) + ve;  // off-line column sums at x
+        co[c] = (tpo[c] + tno[c]) + vo;
       }
-      line_neighbours<T, NCH>(cc, cl, cr, lane);
+      prev_of<T, NC>(co, sh, lane);  // cc(x-1) at even x
 #pragma unroll
-      for (int c = 0; c < NCH; ++c) P[c] = (cl[c] + cc[c]) + cr[c];
+      for (int c = 0; c < NC; ++c) PE[c] = (sh[c] + ce[c]) + co[c];
+      next_of<T, NC>(ce, sh, lane);  // cc(x+1) at odd x
+#pragma unroll
+      for (int c = 0; c < NC; ++c) PO[c] = (ce[c] + co[c]) + sh[c];
     }
     const long rowbase = (long)zz * sxy + (long)y * nx;
-    T own[NCH], rr[NCH];
+    T E[NC], O[NC], rE[NC], rO[NC];
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      const int x = lane + 32 * c;
-      own[c] = x < nx ? zg[rowbase + x] : T(0);
-      rr[c] = x < nx ? rg[rowbase + x] : T(0);
+    for (int c = 0; c < NC; ++c) {
+      const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+      E[c] = (xe < nx && own_valid) ? zg[rowbase + xe] : T(0);
+      O[c] = (xo < nx && own_valid) ? zg[rowbase + xo] : T(0);
+      rE[c] = xe < nx ? rg[rowbase + xe] : T(0);
+      rO[c] = xo < nx ? rg[rowbase + xo] : T(0);
     }
+    T nb[NC];  // neighbours along x of the parity updated last
     for (int s = 0; s < steps; ++s) {
       const int q = (s & 1) ? 1 - pa : pa;
-      T ol[NCH], orr[NCH];
-      line_neighbours<T, NCH>(own, ol, orr, lane);
+      if (q == 0) {
+        prev_of<T, NC>(O, nb, lane);
 #pragma unroll
-      for (int c = 0; c < NCH; ++c) {
-        const int x = lane + 32 * c;
-        if (x < nx && (x & 1) == q) {
-          const T id = invd ? invd[g.off + rowbase + x] : T(1) / T(26);
-          own[c] = (((rr[c] + P[c]) + ol[c]) + orr[c]) * id;
+        for (int c = 0; c < NC; ++c) {
+          const int xe = 2 * (lane + 32 * c);
+          if (xe < nx) {
+            const T id = invd ? invd[g.off + rowbase + xe] : T(1) / T(26);
+            E[c] = (((rE[c] + PE[c]) + nb[c]) + O[c]) * id;
+          }
+        }
+      } else {
+        next_of<T, NC>(E, nb, lane);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int xo = 2 * (lane + 32 * c) + 1;
+          if (xo < nx) {
+            const T id = invd ? invd[g.off + rowbase + xo] : T(1) / T(26);
+            O[c] = (((rO[c] + PO[c]) + E[c]) + nb[c]) * id;
+          }
+        }
+      }
+    }
+    const bool write_e = steps > 1 || !own_valid || pa == 0;
+    const bool write_o = steps > 1 || !own_valid || pa == 1;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+      if (write_e && xe < nx) zg[rowbase + xe] = E[c];
+      if (write_o && xo < nx) zg[rowbase + xo] = O[c];
+    }
+    if (rc) {
+      // the last step updated even x; nb holds its (unchanged) left odd neighbours
+      const Inst gc = tabc[ii];
+      const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 2 * (lane + 32 * c);
+        if (xe < nx) {
+          const T d = kap ? T(26) + kap[g.off + rowbase + xe] : T(26);
+          const T nbs = (PE[c] + nb[c]) + O[c];
+          rc[cbase + (xe >> 1)] = rE[c] - (d * E[c] - nbs);
         }
       }
     }
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      const int x = lane + 32 * c;
-      if (x < nx && (steps > 1 || (x & 1) == pa)) zg[rowbase + x] = own[c];
+    for (int c = 0; c < NC; ++c) {
+      tpe[c] = tne[c];
+      tpo[c] = tno[c];
     }
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) tprev[c] = tnext[c];
   }
 }
 
 // y = A x (Mode 0) or y = b - A x (Mode 1) over every x-line; A x = (27 + kappa) x - S
 // with S the 27-point box sum.  Block = 32 x lpc threads (lpc consecutive lines
-// in y), zc consecutive planes.  Optional partials of x.y per block.
+// in y), zc consecutive planes.  Optional partials of x.y, one per x-line
+// (index poff + z ny + y), so the reduction does not depend on the launch shape.
 template <typename T, int NCH, int Mode>
 __global__ void __launch_bounds__(256) k_spmv_lines(const Inst *__restrict__ tab, int count, int lpc, int zc, const T *__restrict__ x,
                                                     const T *__restrict__ b, T *__restrict__ y, const T *__restrict__ kap,
                                                     double *__restrict__ partials, const CgState *__restrict__ st) {
-  __shared__ double sh[8];
   const int blk = blockIdx.x;
   const int ii = find_inst<3>(tab, count, blk);
   const Inst g = tab[ii];
@@ -160,7 +263,6 @@ __global__ void __launch_bounds__(256) k_spmv_lines(const Inst *__restrict__ tab
   const int nx = g.nx;
   const long sxy = (long)nx * g.ny;
   const T *xg = x + g.off;
-  double dotv = 0.0;
   if (!skip && yy < g.ny && z0 < z1) {
     T t0[NCH], t1[NCH];
     tsum<T, NCH>(xg, nx, g.ny, g.nz, yy, z0 - 1, lane, t0);
@@ -172,6 +274,7 @@ __global__ void __launch_bounds__(256) k_spmv_lines(const Inst *__restrict__ tab
       for (int c = 0; c < NCH; ++c) u[c] = (t0[c] + t1[c]) + t2[c];
       line_neighbours<T, NCH>(u, ul, ur, lane);
       const long rowbase = (long)zz * sxy + (long)yy * nx;
+      double dotv = 0.0;
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
         const int xx = lane + 32 * c;
@@ -186,6 +289,11 @@ __global__ void __launch_bounds__(256) k_spmv_lines(const Inst *__restrict__ tab
           if (partials) dotv += (double)xi * (double)out;
         }
       }
+      if (partials) {  // fixed shuffle tree over the lanes of this line
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dotv += __shfl_down_sync(kFull, dotv, o);
+        if (lane == 0) partials[g.poff + (long)zz * g.ny + yy] = dotv;
+      }
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
         t0[c] = t1[c];
@@ -193,17 +301,11 @@ __global__ void __launch_bounds__(256) k_spmv_lines(const Inst *__restrict__ tab
       }
     }
   }
-  if (partials) {
-    // fixed-order block sum over (lane, line)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dotv += __shfl_down_sync(kFull, dotv, o);
-    if (lane == 0) sh[threadIdx.y] = dotv;
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)blockDim.y; ++w) s += sh[w];
-      partials[blk] = s;
-    }
+  if (skip && partials) {
+    // a converged instance still owns its partial slots: zero them
+    if (yy < g.ny)
+      for (int zz = z0 + 0; zz < z1; ++zz)
+        if (lane == 0) partials[g.poff + (long)zz * g.ny + yy] = 0.0;
   }
 }
 

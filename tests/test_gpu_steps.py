@@ -2,6 +2,7 @@
 through the C ABI.  Index maps bit-exact; FP64 outputs within 1e-12 normwise."""
 import numpy as np
 import pytest
+import torch
 
 from hpcg_inputs import normal, uniform
 from oracle import OracleProblem
@@ -115,3 +116,41 @@ def test_dot_is_deterministic():
     a, b = dev(normal(3000017, 5)), dev(normal(3000017, 6))
     vals = {float(host(g.dot(a, b))[0]) for _ in range(5)}
     assert len(vals) == 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_vcycle_ignores_stale_buffers(precision):
+    """The V-cycle starts every level from z = 0 without clearing memory first:
+    lines not yet written count as zero.  A NaN-filled output and a workspace
+    left over from a previous call must not leak into the result."""
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    from tests.gpu_util import TOL32
+    dims, levels = (32, 24, 16), 3
+    n = int(np.prod(dims))
+    g = HpcgProblem(*dims, levels=levels, precision=precision)
+    o = OracleProblem(*dims, levels=levels)
+    tol = TOL64 if precision == "fp64" else TOL32
+    z = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    for seed in (1, 2):
+        r = normal(n, seed)
+        g.mg_vcycle(dev(r), out=z)
+        assert normwise(host(z), o.mg(r)) <= tol
+
+
+def test_autotune_keeps_results():
+    """Every launch shape the tuner may pick gives the same bits."""
+    import ctypes
+    from paper_2304_08232_gb300 import HpcgProblem, _lib
+    need_gpu()
+    dims = (48, 32, 40)
+    n = int(np.prod(dims))
+    g = HpcgProblem(*dims, levels=3)
+    r = dev(normal(n, 4))
+    z1 = host(g.mg_vcycle(r))
+    shapes = (ctypes.c_int * 12)()
+    lib = _lib.load()
+    assert lib.hpcg_autotune(g.h, shapes, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    assert all(v >= 1 for v in shapes)
+    z2 = host(g.mg_vcycle(r))
+    np.testing.assert_array_equal(z1, z2)
