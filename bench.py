@@ -123,6 +123,14 @@ def dist_env():
     return world, rank, local
 
 
+def persistent_first(prob):
+    import ctypes
+    from paper_2304_08232_gb300 import _lib
+    v = ctypes.c_int()
+    _lib.load().hpcg_persistent_levels(prob.h, ctypes.byref(v))
+    return v.value
+
+
 def tuned_shapes(prob):
     """Launch shapes the library's autotuner picked, per level:
     [row lines, row planes, colour-line lines, colour-line planes]."""
@@ -385,6 +393,21 @@ def run_gpu(args):
         res[prec] = {"ms": t0.elapsed_time(t1), "iters": st.iters, "restarts": st.restarts, "rel_res": st.rel_res,
                      "true_rel_res": true_rel, "err_vs_xtrue": float((xs - xt).abs().max() / xt.abs().max()),
                      "x": xs}
+    # the same FP64 solve with the smallest levels in one persistent cooperative kernel
+    p_np = HpcgProblem(NX, NY, NZ, levels=LEVELS, persistent=True, device=dev)
+    xnp = torch.zeros(n, dtype=torch.float64, device=dev)
+    p_np.pcg_solve(b, max_iters=ITERS, tol=0.0, out=xnp)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    xnp.zero_()
+    p_np.pcg_solve(b, max_iters=ITERS, tol=0.0, out=xnp)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    persistent_ms = t0.elapsed_time(t1)
+    persistent_first_level = persistent_first(p_np)
+    del p_np, xnp
     mixed_vs = {k: {kk: vv for kk, vv in v.items() if kk != "x"} for k, v in res.items()}
     mixed_vs["speedup"] = res["fp64"]["ms"] / res["mixed"]["ms"]
     mixed_vs["mixed_vs_fp64_x"] = float((res["mixed"]["x"] - res["fp64"]["x"]).abs().max() / res["fp64"]["x"].abs().max())
@@ -446,6 +469,8 @@ def run_gpu(args):
         "hbm_peak": {"value": peaks.get("hbm_gbs"), "kind": kind},
         "mixed_vs_fp64_to_1e-9": mixed_vs,
         "spmv": spmv,
+        "fp64_solve_ms_with_persistent_coarse_kernel": {"ms_per_step": persistent_ms,
+                                                          "first_level": persistent_first_level},
         "forms": forms,
         "e2e": e2e,
         "clocks": clocks,

@@ -68,6 +68,9 @@ typedef struct {
   int max_rhs;      /* largest nrhs of hpcg_pcg_solve_multi the workspace is sized for (default 0) */
   int autotune;     /* 1 (default): the first compute call times candidate launch shapes of the
                        line kernels on every level and keeps the fastest (hpcg_autotune) */
+  int persistent;   /* 1: the smallest levels of the V-cycle run in one persistent cooperative
+                       kernel (hpcg_persistent_levels); 0 (default): one launch per step, which
+                       measured faster on one 192^3 grid (graph launches beat grid barriers) */
 } hpcg_options;
 
 typedef struct {
@@ -212,6 +215,24 @@ int hpcg_autotune(hpcg_handle h, int *shapes_host, void *stream);
  * handle as tuned.  Errors: INVALID_ARG for a null pointer or a value out of
  * range. */
 int hpcg_set_launch_shapes(hpcg_handle h, const int *shapes_host);
+
+/* --- persistent coarse levels and bounded waits ----------------------------------------- */
+/* The smallest levels of the V-cycle (those whose x-lines fit one 32-wide chunk
+ * per parity, up to 50,000 rows over all instances) run in one persistent
+ * cooperative kernel whose phases are separated by grid barriers.  Every
+ * barrier wait is bounded by a number of SM clock cycles (default 2e9, about
+ * one second); a wait that runs out makes the kernel record HPCG_ERR_TIMEOUT,
+ * mark every instance's solve as finished and return, leaving the context
+ * usable.  hpcg_set_wait_limit changes the bound (0 makes any wait time out:
+ * a host-side way to exercise the error path).  Not part of the paper. */
+int hpcg_set_wait_limit(hpcg_handle h, long long cycles);
+/* Synchronises the device and reports HPCG_ERR_TIMEOUT in *status_out if a
+ * bounded wait of the handle's kernels ran out since the last solve or
+ * V-cycle started, HPCG_OK otherwise. */
+int hpcg_device_status(hpcg_handle h, int *status_out);
+/* First level run by the persistent kernel, or -1 when every level uses one
+ * launch per step. */
+int hpcg_persistent_levels(hpcg_handle h, int *first_level);
 
 /* --- allocation-free V-cycle ---------------------------------------------------------- */
 /* No counterpart in the paper: a convenience for callers that cannot allocate

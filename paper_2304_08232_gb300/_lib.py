@@ -16,7 +16,8 @@ _d = ctypes.c_double
 
 class hpcg_options(ctypes.Structure):
     _fields_ = [("nx", _i), ("ny", _i), ("nz", _i), ("levels", _i), ("precision", _i), ("pre_sweeps", _i),
-                ("post_sweeps", _i), ("symmetric", _i), ("check_every", _i), ("max_rhs", _i), ("autotune", _i)]
+                ("post_sweeps", _i), ("symmetric", _i), ("check_every", _i), ("max_rhs", _i), ("autotune", _i),
+                ("persistent", _i)]
 
 
 class hpcg_stats(ctypes.Structure):
@@ -55,6 +56,9 @@ SIGNATURES = {
     "hpcg_mg_vcycle_noalloc": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
     "hpcg_autotune": (_i, [_vp, ctypes.POINTER(_i), _vp]),
     "hpcg_set_launch_shapes": (_i, [_vp, ctypes.POINTER(_i)]),
+    "hpcg_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
+    "hpcg_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
+    "hpcg_persistent_levels": (_i, [_vp, ctypes.POINTER(_i)]),
     "hpcg_strerror": (ctypes.c_char_p, [_i]),
     "hpcg_last_cuda_error": (ctypes.c_char_p, []),
     "hpcg_launch_count": (_l, []),

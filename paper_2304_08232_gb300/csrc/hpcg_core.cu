@@ -14,6 +14,7 @@
 #include "hpcg_ctx.h"
 #include "hpcg_kernels.cuh"
 #include "hpcg_lines.cuh"
+#include "hpcg_tail.cuh"
 
 using namespace hpcg;
 
@@ -166,6 +167,8 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
   h->npart = (size_t)std::max(std::max((long)std::max(L0.tab.nblk_full, L0.tab.nblk_red), max_row_blocks), (long)kRawDotBlocks) + 64;
   h->o_part = take(sizeof(double) * h->npart);
   h->o_out = take(sizeof(double) * (h->count + 64));
+  h->o_tail = take(2 * sizeof(TailPlan));
+  h->o_sync = take(64);
   const long n0 = L0.n;
   h->o_cg = take(sizeof(double) * 4 * (size_t)n0);
   const bool mixed = h->opt.precision == HPCG_MIXED;
@@ -188,19 +191,23 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
   }
   h->multi_bytes = 0;
   if (h->opt.max_rhs > 0 && h->batch == 0) {
-    // multi-RHS region (carved by hpcg_multi.cu for the actual nrhs <= max_rhs):
-    // interleaved X B r z p Ap (6 n0 R), level vectors r z (l >= 1), per-rhs
-    // partials of the fixed reduction grid, states and histories
-    const size_t R = (size_t)h->opt.max_rhs;
-    size_t b = 6 * align256(sizeof(double) * (size_t)n0 * R);
-    for (int l = 1; l < h->levels; ++l) b += 2 * align256(sizeof(double) * (size_t)h->lv[l].n * R);
-    b += align256(sizeof(double) * R * 1184) + align256(sizeof(CgState) * R) + align256(sizeof(double) * R * kHistoryCap);
-    h->o_multi = take(b);
-    h->multi_bytes = b;
+    // multi-RHS solves run as a batch of copies of this grid whose workspace
+    // is this region (sized for max_rhs copies)
+    hpcg_ctx tmp;
+    tmp.opt = h->opt;
+    tmp.opt.max_rhs = 0;
+    tmp.batch = 1;
+    tmp.levels = h->levels;
+    std::vector<int> rep;
+    for (int k = 0; k < h->opt.max_rhs; ++k) rep.insert(rep.end(), dims.begin(), dims.begin() + 3);
+    plan(&tmp, rep);
+    h->multi_bytes = tmp.need;
+    h->o_multi = take(h->multi_bytes);
   }
   h->need = off;
 }
 
+static int build_tail_plans(hpcg_ctx *h);
 static int bind(hpcg_ctx *h, char *ws, size_t bytes, bool owned) {
   if (bytes < h->need) return HPCG_ERR_NO_WORKSPACE;
   if (((uintptr_t)ws & 255) != 0) return HPCG_ERR_INVALID_ARG;
@@ -237,16 +244,19 @@ static int bind(hpcg_ctx *h, char *ws, size_t bytes, bool owned) {
     cudaGraphExecDestroy(h->g_iter.exec);
     h->g_iter = GraphCache{};
   }
-  if (h->g_multi.exec) {  // captured with pointers into the previous workspace
-    cudaGraphExecDestroy(h->g_multi.exec);
-    h->g_multi = GraphCache{};
+  if (h->multi) {  // its workspace was a region of the previous one
+    hpcg_destroy(h->multi);
+    h->multi = nullptr;
+    h->multi_R = 0;
   }
   h->ready = true;
-  return HPCG_OK;
+  CK(cudaMemset(ws + h->o_sync, 0, 64));
+  return build_tail_plans(h);
 }
 
 static int set_kappa_impl(hpcg_ctx *h, const double *kappa, cudaStream_t s);
 static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s);
+static int build_tail_plans(hpcg_ctx *h);
 
 int ensure_ready(hpcg_ctx *h, cudaStream_t s) {
   if (!h->ready) {
@@ -281,7 +291,7 @@ static int set_kappa_impl(hpcg_ctx *h, const double *kappa, cudaStream_t s) {
   if (h->batch) return HPCG_ERR_UNSUPPORTED;
   if (!kappa) {
     h->has_kappa = false;
-    return HPCG_OK;
+    return build_tail_plans(h);
   }
   LevelData &L0 = h->lv[0];
   CK(cudaMemcpyAsync(L0.kap, kappa, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, s));
@@ -297,6 +307,117 @@ static int set_kappa_impl(hpcg_ctx *h, const double *kappa, cudaStream_t s) {
     CKL("k_kappa_derived");
   }
   h->has_kappa = true;
+  return build_tail_plans(h);
+}
+
+// ---------------------------------------------------------------------------
+static std::vector<int> phase_sequence(int sweeps, int symmetric);
+
+// Runs of one line class (see enqueue_smoother) of a smoother application.
+static int make_runs(int sweeps, int symmetric, TailRun *out, int cap) {
+  const std::vector<int> seq = phase_sequence(sweeps, symmetric);
+  int nr = 0;
+  size_t i = 0;
+  while (i < seq.size()) {
+    size_t j = i + 1;
+    while (j < seq.size() && (seq[j] >> 1) == (seq[i] >> 1)) ++j;
+    if (nr >= cap) return -1;
+    out[nr].cls = (signed char)(seq[i] >> 1);
+    out[nr].pa = (signed char)(seq[i] & 1);
+    out[nr].steps = (signed char)(j - i);
+    out[nr].pad = 0;
+    ++nr;
+    i = j;
+  }
+  return nr;
+}
+
+// Chooses the levels of the persistent tail (small levels whose lines fit one
+// 32-wide chunk per parity) and writes the FP64 and FP32 tail plans.
+static int build_tail_plans(hpcg_ctx *h) {
+  h->tail_first = -1;
+  if (!h->tail_ok || !h->opt.persistent || h->levels < 2) return HPCG_OK;
+  int first = h->levels;
+  for (int l = h->levels - 1; l >= 1; --l) {
+    const LevelTab &t = h->lv[l].tab;
+    if (t.nch == 0 || t.nch2 != 1 || h->lv[l].n > 50000) break;
+    first = l;
+  }
+  if (first >= h->levels) return HPCG_OK;
+  for (int prec = 0; prec < 2; ++prec) {
+    if (prec == 1 && h->opt.precision != HPCG_MIXED) continue;
+    TailPlan P;
+    memset(&P, 0, sizeof(P));
+    P.first = first;
+    P.last = h->levels - 1;
+    P.count = h->count;
+    for (int l = first; l < h->levels; ++l) {
+      const LevelData &L = h->lv[l];
+      TailLevel &T = P.lv[l];
+      T.tab = L.tab.inst;
+      T.r = prec == 0 ? (void *)L.r : (void *)L.r32;
+      T.z = prec == 0 ? (void *)L.z : (void *)L.z32;
+      T.invd = h->has_kappa ? (prec == 0 ? (const void *)L.invd : (const void *)L.invd32) : nullptr;
+      T.kap = h->has_kappa ? (prec == 0 ? (const void *)L.kap : (const void *)L.kap32) : nullptr;
+      T.lpc = L.tab.line_lpc;
+      T.zc = L.tab.line_zc;
+      T.nvb = L.tab.nblk_line;
+      const bool coarsest = l == h->levels - 1;
+      T.npre = make_runs(coarsest ? 1 : h->opt.pre_sweeps, h->opt.symmetric, T.pre, kTailRuns);
+      T.npost = coarsest ? 0 : make_runs(h->opt.post_sweeps, h->opt.symmetric, T.post, kTailRuns);
+      if (T.npre < 0 || T.npost < 0) return HPCG_OK;  // too many runs: no tail
+      const TailRun last = T.pre[T.npre - 1];
+      const int last_parity = (last.steps & 1) ? last.pa : 1 - last.pa;
+      T.fuse = (!coarsest && last.cls == 0 && last_parity == 0) ? 1 : 0;
+    }
+    CK(cudaMemcpy(h->ws + h->o_tail + prec * sizeof(TailPlan), &P, sizeof(P), cudaMemcpyHostToDevice));
+  }
+  int dev = 0, sms = 0, occ = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vcycle_tail<double>, 32 * kTailThreadsY, 0));
+  int occ32 = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_vcycle_tail<float>, 32 * kTailThreadsY, 0));
+  occ = std::min(occ, occ32);
+  if (occ < 1) return HPCG_OK;
+  // just enough blocks to take the largest phase in one round (fewer blocks
+  // make every grid barrier cheaper), one per SM at most so all are resident
+  int need = 1;
+  for (int l = first; l < h->levels; ++l) {
+    const LevelTab &t = h->lv[l].tab;
+    const int vpb = std::max(1, kTailThreadsY / t.line_lpc);
+    need = std::max(need, (t.nblk_line + vpb - 1) / vpb);
+  }
+  h->tail_grid = std::min(sms, need);
+  h->tail_first = first;
+  return HPCG_OK;
+}
+
+// Launches the tail for precision T (0: FP64 plan, 1: FP32 plan) as a cooperative kernel.
+template <typename T>
+static int enqueue_tail(hpcg_ctx *h, cudaStream_t s, const CgState *st) {
+  unsigned *bar = (unsigned *)(h->ws + h->o_sync);
+  int *err = (int *)(bar + 2);
+  const TailPlan *plan = (const TailPlan *)(h->ws + h->o_tail + (sizeof(T) == 4 ? sizeof(TailPlan) : 0));
+  CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(h->tail_grid);
+  cfg.blockDim = dim3(32, kTailThreadsY);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<T>, plan, bar, err, h->wait_limit, const_cast<CgState *>(st));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (e != cudaSuccess) return cuda_fail(e, "k_vcycle_tail (cooperative launch)");
+  return HPCG_OK;
+}
+
+static int reset_error_word(hpcg_ctx *h, cudaStream_t s) {
+  CK(cudaMemsetAsync(h->ws + h->o_sync + 2 * sizeof(unsigned), 0, sizeof(int), s));
   return HPCG_OK;
 }
 
@@ -464,6 +585,20 @@ static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s
 template <typename T>
 static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_t s, const CgState *st) {
   const int L = h->levels;
+  if (h->tail_first > 0) {
+    const int first = h->tail_first;
+    for (int l = 0; l < first; ++l) {
+      bool fused = false;
+      TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], h->opt.pre_sweeps, s, st, true, rl[l + 1], &fused));
+      if (!fused) TRY(enqueue_restrict<T>(h, l, rl[l], zl[l], rl[l + 1], s, st));
+    }
+    TRY(enqueue_tail<T>(h, s, st));  // levels first..L-1 and back up to `first`
+    for (int l = first - 1; l >= 0; --l) {
+      TRY(enqueue_prolong<T>(h, l, zl[l + 1], zl[l], s, st));
+      TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], h->opt.post_sweeps, s, st));
+    }
+    return HPCG_OK;
+  }
   for (int l = 0; l < L; ++l) {
     // z <- 0 and pre-smoothing; on the way down the residual restriction
     // r_c <- restrict(r - A z) is fused into the smoother's last run when it
@@ -527,7 +662,7 @@ static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_ite
   TRY((enqueue_spmv<double, 1>(h, 0, x, b, h->cg_r, h->has_kappa ? L0.kap : nullptr, nullptr, nullptr, s)));
   k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_r, h->part, h->st);
   CKL("k_dot_partial");
-  k_finalize<FIN_NORM0><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  k_finalize<FIN_NORM0><<<h->count, kFinThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<NORM0>");
   if (max_iters <= 0) {
     // nothing to iterate: mark every instance done
@@ -545,16 +680,16 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st));  // z = M r
   k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_z, h->part, h->st);
   CKL("k_dot_partial");
-  k_finalize<FIN_RTZ><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  k_finalize<FIN_RTZ><<<h->count, kFinThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<RTZ>");
   k_update_p<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_z, h->cg_p, h->st);  // p = z + beta p
   CKL("k_update_p");
   TRY((enqueue_spmv<double, 0>(h, 0, h->cg_p, nullptr, h->cg_ap, kap, h->part, h->st, s)));  // Ap, p.Ap partials
-  k_finalize<FIN_PAP><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, L0.tab.nch ? 2 : 1, h->st, h->hist, nullptr);
+  k_finalize<FIN_PAP><<<h->count, kFinThreads, 0, s>>>(L0.tab.inst, h->count, h->part, L0.tab.nch ? 2 : 1, h->st, h->hist, nullptr);
   CKL("k_finalize<PAP>");
   k_update_xr<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r, h->part, h->st);
   CKL("k_update_xr");
-  k_finalize<FIN_NORM><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  k_finalize<FIN_NORM><<<h->count, kFinThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<NORM>");
   return HPCG_OK;
 }
@@ -572,18 +707,28 @@ static int get_iter_graph(hpcg_ctx *h, const double *b, double *x, cudaGraphExec
     g.exec = nullptr;
   }
   if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
-  cudaGraph_t graph;
-  const long before = g_launches.load();
-  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_pcg_iter(h, b, x, h->cap);
-  cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
-  if (rc != HPCG_OK) return rc;
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  const long nk = g_launches.load() - before;
-  g_launches.fetch_sub(nk);  // counted again at every replay
-  e = cudaGraphInstantiate(&g.exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  long nk = 0;
+  for (int attempt = 0;; ++attempt) {
+    cudaGraph_t graph = nullptr;
+    const long before = g_launches.load();
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_pcg_iter(h, b, x, h->cap);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    nk = g_launches.load() - before;
+    g_launches.fetch_sub(nk);  // counted again at every replay
+    if (rc == HPCG_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc == HPCG_OK && e == cudaSuccess) break;
+    cudaGetLastError();
+    if (attempt == 0 && h->tail_first > 0) {
+      // a cooperative launch the capture refused: fall back to one launch per step
+      h->tail_ok = false;
+      TRY(build_tail_plans(h));
+      continue;
+    }
+    if (rc != HPCG_OK) return rc;
+    return cuda_fail(e, "iteration graph capture");
+  }
   g.key[0] = b;
   g.key[1] = x;
   g.kernels = nk;
@@ -594,6 +739,7 @@ static int get_iter_graph(hpcg_ctx *h, const double *b, double *x, cudaGraphExec
 
 static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, double tol, hpcg_stats *stats, cudaStream_t s) {
   if (max_iters < 0 || max_iters > kHistoryCap) return HPCG_ERR_INVALID_ARG;
+  TRY(reset_error_word(h, s));
   TRY(enqueue_pcg_init(h, b, x, max_iters, tol, s));
   cudaGraphExec_t exec;
   long nk = 0;
@@ -668,9 +814,12 @@ static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, doubl
         CK(cudaMemcpy(o.history, h->hist + (size_t)i * kHistoryCap, sizeof(double) * m, cudaMemcpyDeviceToHost));
       }
     }
-    if (st == HPCG_ERR_BREAKDOWN) worst = st;
+    if (st == HPCG_ERR_TIMEOUT || (st == HPCG_ERR_BREAKDOWN && worst != HPCG_ERR_TIMEOUT)) worst = st;
     else if (st != HPCG_OK && worst == HPCG_OK) worst = st;
   }
+  int err = 0;
+  CK(cudaMemcpy(&err, h->ws + h->o_sync + 2 * sizeof(unsigned), sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) worst = HPCG_ERR_TIMEOUT;
   return worst;
 }
 
@@ -767,12 +916,41 @@ static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s) {
     h->g_iter = GraphCache{};
   }
   h->tuned = true;
-  return HPCG_OK;
+  return build_tail_plans(h);
 }
 
 // ---------------------------------------------------------------------------
 // C ABI
 extern "C" {
+
+int hpcg_set_wait_limit(hpcg_handle h, long long cycles) {
+  if (!h || cycles < 0) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->wait_limit = cycles;
+  if (h->g_iter.exec) {  // the limit is a kernel argument of the captured graph
+    cudaGraphExecDestroy(h->g_iter.exec);
+    h->g_iter = GraphCache{};
+  }
+  return HPCG_OK;
+}
+
+int hpcg_device_status(hpcg_handle h, int *status_out) {
+  if (!h || !status_out) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  *status_out = HPCG_OK;
+  if (!h->ready) return HPCG_OK;
+  CK(cudaDeviceSynchronize());
+  int err = 0;
+  CK(cudaMemcpy(&err, h->ws + h->o_sync + 2 * sizeof(unsigned), sizeof(int), cudaMemcpyDeviceToHost));
+  *status_out = err ? HPCG_ERR_TIMEOUT : HPCG_OK;
+  return HPCG_OK;
+}
+
+int hpcg_persistent_levels(hpcg_handle h, int *first_level) {
+  if (!h || !first_level) return HPCG_ERR_INVALID_ARG;
+  *first_level = h->tail_first;
+  return HPCG_OK;
+}
 
 int hpcg_set_launch_shapes(hpcg_handle h, const int *shapes_host) {
   if (!h || !shapes_host) return HPCG_ERR_INVALID_ARG;
@@ -796,7 +974,7 @@ int hpcg_set_launch_shapes(hpcg_handle h, const int *shapes_host) {
     h->g_iter = GraphCache{};
   }
   h->tuned = true;
-  return HPCG_OK;
+  return h->ready ? build_tail_plans(h) : HPCG_OK;
 }
 
 int hpcg_autotune(hpcg_handle h, int *shapes_host, void *stream) {
@@ -825,6 +1003,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->check_every = 1;
   opt->max_rhs = 0;
   opt->autotune = 1;
+  opt->persistent = 0;
   return HPCG_OK;
 }
 
@@ -894,7 +1073,7 @@ int hpcg_destroy(hpcg_handle h) {
   if (!h) return HPCG_ERR_INVALID_ARG;
   if (h->ready) cudaDeviceSynchronize();
   if (h->g_iter.exec) cudaGraphExecDestroy(h->g_iter.exec);
-  if (h->g_multi.exec) cudaGraphExecDestroy(h->g_multi.exec);
+  if (h->multi) hpcg_destroy(h->multi);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ws_owned && h->ws) cudaFree(h->ws);
   delete h;
@@ -1006,6 +1185,7 @@ int hpcg_mg_vcycle(hpcg_handle h, const double *r_dev, double *z_dev, void *stre
   std::lock_guard<std::mutex> lk(h->mu);
   cudaStream_t s = (cudaStream_t)stream;
   TRY(ensure_ready(h, s));
+  TRY(reset_error_word(h, s));
   return enqueue_vcycle(h, r_dev, z_dev, s, nullptr);
 }
 
@@ -1038,6 +1218,39 @@ int hpcg_pcg_solve(hpcg_handle h, const double *b_dev, double *x_dev, int max_it
   cudaStream_t s = (cudaStream_t)stream;
   TRY(ensure_ready(h, s));
   return run_pcg(h, b_dev, x_dev, max_iters, rel_tol, stats, s);
+}
+
+int hpcg_pcg_solve_multi(hpcg_handle h, int nrhs, const double *B_dev, double *X_dev, int max_iters, double rel_tol,
+                         hpcg_stats *stats, void *stream) {
+  if (!h || !B_dev || !X_dev || nrhs < 1 || nrhs > 64) return HPCG_ERR_INVALID_ARG;
+  if (h->batch) return HPCG_ERR_UNSUPPORTED;
+  if (nrhs > h->opt.max_rhs) return HPCG_ERR_NO_WORKSPACE;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  if (h->has_kappa) return HPCG_ERR_UNSUPPORTED;  // the copies carry no diagonal field
+  if (!h->multi || h->multi_R != nrhs) {
+    if (h->multi) hpcg_destroy(h->multi);
+    h->multi = nullptr;
+    std::vector<int> rep;
+    const Inst &g = h->lv[0].inst[0];
+    for (int k = 0; k < nrhs; ++k) rep.insert(rep.end(), {g.nx, g.ny, g.nz});
+    hpcg_options o = h->opt;
+    o.max_rhs = 0;
+    hpcg_handle m = nullptr;
+    TRY(make_handle(&o, rep, 1, &m));
+    int rc = bind(m, h->ws + h->o_multi, h->multi_bytes, false);
+    if (rc != HPCG_OK) {
+      delete m;
+      return rc;
+    }
+    h->multi = m;
+    h->multi_R = nrhs;
+  }
+  std::lock_guard<std::mutex> lk2(h->multi->mu);
+  TRY(ensure_ready(h->multi, s));
+  // the [nrhs][n] arrays are exactly the batch's concatenated vectors
+  return run_pcg(h->multi, B_dev, X_dev, max_iters, rel_tol, stats, s);
 }
 
 int hpcg_pcg_solve_batch(hpcg_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol, hpcg_stats *stats,

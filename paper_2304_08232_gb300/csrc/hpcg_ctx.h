@@ -78,8 +78,15 @@ struct hpcg_ctx {
   size_t o_multi = 0, multi_bytes = 0;
   cudaStream_t cap = nullptr;
   GraphCache g_iter;
-  GraphCache g_multi;
+  hpcg_ctx *multi = nullptr;  // internal batch of max_rhs copies of the grid (hpcg_pcg_solve_multi)
+  int multi_R = 0;
   bool tuned = false;
+  // persistent tail of the V-cycle (levels tail_first..levels-1 in one cooperative launch)
+  int tail_first = -1;        // -1: no tail
+  bool tail_ok = true;        // cleared if a cooperative launch is refused
+  int tail_grid = 0;
+  long long wait_limit = 2000000000LL;  // clock cycles a grid barrier may wait (about 1 s)
+  size_t o_tail = 0, o_sync = 0;        // TailPlan[2] (FP64, FP32) and {barrier count, generation, error}
   int device = 0;
   std::mutex mu;
 };

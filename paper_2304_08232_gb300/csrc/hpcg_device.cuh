@@ -62,22 +62,22 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 }
 
 // Fixed-order sum of partials[first .. first+cnt) inside one block; valid in
-// thread 0.  Thread t sums elements t + k*blockDim in four interleaved
+// thread 0.  Thread t sums elements t + k*blockDim in eight interleaved
 // accumulators (independent load/add chains), combined in a fixed order.
 __device__ __forceinline__ double sum_partials(const double *__restrict__ partials, int first, int cnt, double *sh) {
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = 0.0;
   const int bd = blockDim.x;
   int k = threadIdx.x;
-  for (; k + 3 * bd < cnt; k += 4 * bd) {
-    a0 += partials[first + k];
-    a1 += partials[first + k + bd];
-    a2 += partials[first + k + 2 * bd];
-    a3 += partials[first + k + 3 * bd];
+  for (; k + 7 * bd < cnt; k += 8 * bd) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += partials[first + k + j * bd];
   }
-  if (k < cnt) a0 += partials[first + k];
-  if (k + bd < cnt) a1 += partials[first + k + bd];
-  if (k + 2 * bd < cnt) a2 += partials[first + k + 2 * bd];
-  return block_sum((a0 + a1) + (a2 + a3), sh);
+#pragma unroll
+  for (int j = 0; j < 7; ++j)
+    if (k + j * bd < cnt) a[j] += partials[first + k + j * bd];
+  return block_sum(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])), sh);
 }
 
 enum FinKind { FIN_NORM0 = 0, FIN_RTZ = 1, FIN_PAP = 2, FIN_NORM = 3, FIN_OUT = 4 };

@@ -19,6 +19,7 @@ constexpr int kTileX = 32;       // threads of a block along x (one warp)
 constexpr int kTileY = 8;        // warps of a block along y
 constexpr int kBlock = kTileX * kTileY;
 constexpr int kRedThreads = 256; // threads of a reduction block
+constexpr int kFinThreads = 1024; // threads of a finalize block (one per instance)
 constexpr int kRedItems = 8;     // elements per thread per reduction block (before the block strides)
 constexpr int kMaxRedBlocksPerInst = 592;  // 4 x 148... fixed cap keeps reductions deterministic
 constexpr int kHistoryCap = 8192;

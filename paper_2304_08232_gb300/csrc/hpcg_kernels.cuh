@@ -215,10 +215,10 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const Inst *__restr
 // `stencil` selects the stencil blocking (partials written by k_spmv) instead
 // of the reduction blocking.
 template <int Kind>
-__global__ void __launch_bounds__(kRedThreads) k_finalize(const Inst *__restrict__ tab, int count, const double *__restrict__ partials,
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const Inst *__restrict__ tab, int count, const double *__restrict__ partials,
                                                           int stencil, CgState *__restrict__ st, double *__restrict__ hist,
                                                           double *__restrict__ out) {
-  __shared__ double sh[kRedThreads / 32];
+  __shared__ double sh[kFinThreads / 32];
   const int ii = blockIdx.x;
   const Inst g = tab[ii];
   int first, cnt;

@@ -39,6 +39,16 @@ __device__ __forceinline__ void line_neighbours(const T (&v)[NCH], T (&vl)[NCH],
   }
 }
 
+// Loads of z and r.  Kernels launched once per step read lines no one writes
+// during the launch, through the read-only path (COH = false).  The persistent
+// tail kernel reads lines other blocks wrote earlier in the same launch, so it
+// loads at L2 (COH = true), which the grid barrier's fences keep coherent.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_line(const T *p) {
+  if (COH) return __ldcg(p);
+  return __ldg(p);
+}
+
 // Line class of line (y, z): its y and z parities, (y & 1) + 2 (z & 1).
 __device__ __forceinline__ int line_class(int y, int z) { return (y & 1) + 2 * (z & 1); }
 
@@ -94,7 +104,7 @@ __device__ __forceinline__ void next_of(const T (&v)[NC], T (&out)[NC], int lane
 }
 
 // Sum over y-1, y, y+1 of line (., y, zz) at even (te) and odd (to) x.
-template <typename T, int NC>
+template <typename T, int NC, bool COH>
 __device__ __forceinline__ void tsum2(const T *__restrict__ zg, int nx, int ny, int nz, int y, int zz, int lane, T (&te)[NC],
                                       T (&to)[NC], int vmask) {
   const bool zin = zz >= 0 && zz < nz;
@@ -109,8 +119,10 @@ __device__ __forceinline__ void tsum2(const T *__restrict__ zg, int nx, int ny, 
   for (int c = 0; c < NC; ++c) {
     const int xe = 2 * (lane + 32 * c), xo = xe + 1;
     T se = T(0), so = T(0);
-    if (xe < nx) se = ((ym ? __ldg(lm + xe) : T(0)) + (y0 ? __ldg(l0 + xe) : T(0))) + (yp ? __ldg(lp + xe) : T(0));
-    if (xo < nx) so = ((ym ? __ldg(lm + xo) : T(0)) + (y0 ? __ldg(l0 + xo) : T(0))) + (yp ? __ldg(lp + xo) : T(0));
+    if (xe < nx)
+      se = ((ym ? ld_line<COH>(lm + xe) : T(0)) + (y0 ? ld_line<COH>(l0 + xe) : T(0))) + (yp ? ld_line<COH>(lp + xe) : T(0));
+    if (xo < nx)
+      so = ((ym ? ld_line<COH>(lm + xo) : T(0)) + (y0 ? ld_line<COH>(l0 + xo) : T(0))) + (yp ? ld_line<COH>(lp + xo) : T(0));
     te[c] = se;
     to[c] = so;
   }
@@ -126,19 +138,18 @@ __device__ __forceinline__ void tsum2(const T *__restrict__ zg, int nx, int ny, 
 // ends on even x: every injected fine row (2xc, 2yc, 2zc) lies on these lines,
 // its neighbour sum is P + z(x-1) + z(x+1) with values final for this
 // smoother application, so rc[c] = r - (A_ii z - that sum) is formed here.
-template <typename T, int NC>
-__global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
-                                                  int steps, int vmask, const T *__restrict__ r, T *__restrict__ z,
-                                                  const T *__restrict__ invd, const CgState *__restrict__ st, const Inst *__restrict__ tabc,
-                                                  T *__restrict__ rc, const T *__restrict__ kap) {
-  const int blk = blockIdx.x;
+template <typename T, int NC, bool COH = false>
+__device__ __forceinline__ void gs_lines_vblock(int blk, int wy, const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz,
+                                                int pa, int steps, int vmask, const T *__restrict__ r, T *__restrict__ z,
+                                                const T *__restrict__ invd, const CgState *__restrict__ st,
+                                                const Inst *__restrict__ tabc, T *__restrict__ rc, const T *__restrict__ kap) {
   const int ii = find_inst<4>(tab, count, blk);
   const Inst g = tab[ii];
   if (st && st[ii].done) return;
   const int cy = (g.ny - py + 1) / 2, cz = (g.nz - pz + 1) / 2;
   const int nby = (half_up(g.ny) + lpc - 1) / lpc;
   const int lb = blk - g.blk_line;
-  const int j = (lb % nby) * lpc + threadIdx.y;
+  const int j = (lb % nby) * lpc + wy;
   const int m0 = (lb / nby) * zc;
   const int m1 = min(m0 + zc, cz);
   if (j >= cy || m0 >= m1) return;  // whole warp
@@ -152,11 +163,11 @@ __global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, 
   const bool ym = y - 1 >= 0 && ((vmask >> cls_v) & 1), yp = y + 1 < g.ny && ((vmask >> cls_v) & 1);
   const bool own_valid = (vmask >> line_class(y, pz)) & 1;
   T tpe[NC], tpo[NC];
-  tsum2<T, NC>(zg, nx, g.ny, g.nz, y, 2 * m0 + pz - 1, lane, tpe, tpo, vmask);
+  tsum2<T, NC, COH>(zg, nx, g.ny, g.nz, y, 2 * m0 + pz - 1, lane, tpe, tpo, vmask);
   for (int m = m0; m < m1; ++m) {
     const int zz = 2 * m + pz;
     T tne[NC], tno[NC], PE[NC], PO[NC];
-    tsum2<T, NC>(zg, nx, g.ny, g.nz, y, zz + 1, lane, tne, tno, vmask);
+    tsum2<T, NC, COH>(zg, nx, g.ny, g.nz, y, zz + 1, lane, tne, tno, vmask);
     {
       T ce[NC], co[NC], sh[NC];
       const T *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
@@ -165,8 +176,8 @@ __global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, 
       for (int c = 0; c < NC; ++c) {
         const int xe = 2 * (lane + 32 * c), xo = xe + 1;
         T ve = T(0), vo = T(0);
-        if (xe < nx) ve = (ym ? __ldg(lm + xe) : T(0)) + (yp ? __ldg(lp + xe) : T(0));
-        if (xo < nx) vo = (ym ? __ldg(lm + xo) : T(0)) + (yp ? __ldg(lp + xo) : T(0));
+        if (xe < nx) ve = (ym ? ld_line<COH>(lm + xe) : T(0)) + (yp ? ld_line<COH>(lp + xe) : T(0));
+        if (xo < nx) vo = (ym ? ld_line<COH>(lm + xo) : T(0)) + (yp ? ld_line<COH>(lp + xo) : T(0));
         ce[c] = (tpe[c] + tne[c]) + ve;  // off-line column sums at x
         co[c] = (tpo[c] + tno[c]) + vo;
       }
@@ -182,10 +193,10 @@ __global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, 
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int xe = 2 * (lane + 32 * c), xo = xe + 1;
-      E[c] = (xe < nx && own_valid) ? zg[rowbase + xe] : T(0);
-      O[c] = (xo < nx && own_valid) ? zg[rowbase + xo] : T(0);
-      rE[c] = xe < nx ? rg[rowbase + xe] : T(0);
-      rO[c] = xo < nx ? rg[rowbase + xo] : T(0);
+      E[c] = (xe < nx && own_valid) ? (COH ? __ldcg(zg + rowbase + xe) : zg[rowbase + xe]) : T(0);
+      O[c] = (xo < nx && own_valid) ? (COH ? __ldcg(zg + rowbase + xo) : zg[rowbase + xo]) : T(0);
+      rE[c] = xe < nx ? (COH ? __ldcg(rg + rowbase + xe) : rg[rowbase + xe]) : T(0);
+      rO[c] = xo < nx ? (COH ? __ldcg(rg + rowbase + xo) : rg[rowbase + xo]) : T(0);
     }
     T nb[NC];  // neighbours along x of the parity updated last
     for (int s = 0; s < steps; ++s) {
@@ -240,6 +251,14 @@ __global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, 
       tpo[c] = tno[c];
     }
   }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
+                                                  int steps, int vmask, const T *__restrict__ r, T *__restrict__ z,
+                                                  const T *__restrict__ invd, const CgState *__restrict__ st, const Inst *__restrict__ tabc,
+                                                  T *__restrict__ rc, const T *__restrict__ kap) {
+  gs_lines_vblock<T, NC>(blockIdx.x, threadIdx.y, tab, count, lpc, zc, py, pz, pa, steps, vmask, r, z, invd, st, tabc, rc, kap);
 }
 
 // y = A x (Mode 0) or y = b - A x (Mode 1) over every x-line; A x = (27 + kappa) x - S
