@@ -343,19 +343,23 @@ def run_gpu(args):
     sweep_ms = k0.elapsed_time(k1) / reps
     launches_per_sweep = 7
     k_ms = sweep_ms / launches_per_sweep
-    # FP64 instructions per x on the updated lines of one run: plane sums 2 (+2/zc
-    # at a z-chunk start) + 1 (the two lines beside) + 2 (column sum) + 2 (x window)
-    # + 4 per colour step (3 additions, 1 multiply by 1/A_ii)
-    ops_sweep = (n // 4) * (6 * (7 + 2.0 / zc + 2 * 2) + (7 + 2.0 / zc + 2 * 3))
+    # FP64 instructions per x on the updated lines of one run.  The default
+    # kernel (k_gs_lines_fx) sums the 24 off-line neighbours exactly in 64-bit
+    # fixed point on the integer pipe; its FP64 work per x is the conversion of
+    # that sum (1) + 4 per colour step (3 additions, 1 multiply by 1/A_ii):
+    # 5 for a two-step run, 7 for the three-step run [6,7,6].
+    ops_sweep = (n // 4) * (6 * (1 + 2 * 2) + (1 + 2 * 3))
     achieved = ops_sweep / (sweep_ms * 1e-3) / 1e9
     peak_nominal = 152 * 2 * 2070e6 / 1e9  # FP64 instructions per second (2 per SM per clock)
     bytes_launch = 12 * n  # z of every line read once, r and z of the class lines read/written
-    roofline = {"bound": "alu", "kernel": "k_gs_lines<double> (finest level, colour-pair runs of a symmetric sweep)",
+    roofline = {"bound": "alu", "kernel": "k_gs_lines_fx<3> (finest level, colour-pair runs of a symmetric sweep)",
                 "achieved": achieved, "peak": peak_nominal, "unit": "G FP64 instr/s", "frac": achieved / peak_nominal,
                 "peak_basis": "152 SMs x 2 FP64 instructions/clk x 2070 MHz (nominal 1.25 TFLOP/s FMA rate)",
                 "ms_per_launch": k_ms, "ms_per_sweep": sweep_ms, "launches_per_sweep": launches_per_sweep,
                 "fp64_instr_per_sweep": ops_sweep, "hbm_bytes_algorithmic_per_launch": bytes_launch,
-                "hbm_gbs_equivalent": bytes_launch / (k_ms * 1e-3) / 1e9, "traffic": None,
+                "hbm_gbs_equivalent": bytes_launch / (k_ms * 1e-3) / 1e9,
+                "hbm_frac_of_measured": bytes_launch / (k_ms * 1e-3) / 1e9 / measured_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS),
+                "traffic": None,
                 "launch_shapes_per_level": shapes}
     # SpMV line kernel (secondary): 7 + 4/zc FP64 instructions per row
     zr = shapes[0][1]
@@ -393,21 +397,24 @@ def run_gpu(args):
         res[prec] = {"ms": t0.elapsed_time(t1), "iters": st.iters, "restarts": st.restarts, "rel_res": st.rel_res,
                      "true_rel_res": true_rel, "err_vs_xtrue": float((xs - xt).abs().max() / xt.abs().max()),
                      "x": xs}
-    # the same FP64 solve with the smallest levels in one persistent cooperative kernel
-    p_np = HpcgProblem(NX, NY, NZ, levels=LEVELS, persistent=True, device=dev)
-    xnp = torch.zeros(n, dtype=torch.float64, device=dev)
-    p_np.pcg_solve(b, max_iters=ITERS, tol=0.0, out=xnp)
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    xnp.zero_()
-    p_np.pcg_solve(b, max_iters=ITERS, tol=0.0, out=xnp)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    persistent_ms = t0.elapsed_time(t1)
-    persistent_first_level = persistent_first(p_np)
-    del p_np, xnp
+    # the same FP64 solve in other configurations of the library
+    variants = {}
+    for name, kw in [("persistent_coarse_kernel", {"persistent": True}), ("plain_fp64_sums", {"fixed_point": False})]:
+        p_v = HpcgProblem(NX, NY, NZ, levels=LEVELS, device=dev, **kw)
+        xv = torch.zeros(n, dtype=torch.float64, device=dev)
+        p_v.pcg_solve(b, max_iters=ITERS, tol=0.0, out=xv)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        xv.zero_()
+        p_v.pcg_solve(b, max_iters=ITERS, tol=0.0, out=xv)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        variants[name] = {"ms_per_step": t0.elapsed_time(t1), "max_abs_diff_x_vs_default": float((xv - x).abs().max())}
+        if name == "persistent_coarse_kernel":
+            variants[name]["first_level"] = persistent_first(p_v)
+        del p_v, xv
     mixed_vs = {k: {kk: vv for kk, vv in v.items() if kk != "x"} for k, v in res.items()}
     mixed_vs["speedup"] = res["fp64"]["ms"] / res["mixed"]["ms"]
     mixed_vs["mixed_vs_fp64_x"] = float((res["mixed"]["x"] - res["fp64"]["x"]).abs().max() / res["fp64"]["x"].abs().max())
@@ -469,8 +476,7 @@ def run_gpu(args):
         "hbm_peak": {"value": peaks.get("hbm_gbs"), "kind": kind},
         "mixed_vs_fp64_to_1e-9": mixed_vs,
         "spmv": spmv,
-        "fp64_solve_ms_with_persistent_coarse_kernel": {"ms_per_step": persistent_ms,
-                                                          "first_level": persistent_first_level},
+        "fp64_solve_variants": variants,
         "forms": forms,
         "e2e": e2e,
         "clocks": clocks,

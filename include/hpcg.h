@@ -68,6 +68,10 @@ typedef struct {
   int max_rhs;      /* largest nrhs of hpcg_pcg_solve_multi the workspace is sized for (default 0) */
   int autotune;     /* 1 (default): the first compute call times candidate launch shapes of the
                        line kernels on every level and keeps the fastest (hpcg_autotune) */
+  int fixed_point;  /* 1 (default): FP64 colour steps and SpMV sum neighbour values exactly in
+                       64-bit fixed point on the integer pipe (at least as accurate as FP64
+                       summation; FP64 is used for steps with huge or non-finite values);
+                       0: plain FP64 sums */
   int persistent;   /* 1: the smallest levels of the V-cycle run in one persistent cooperative
                        kernel (hpcg_persistent_levels); 0 (default): one launch per step, which
                        measured faster on one 192^3 grid (graph launches beat grid barriers) */

@@ -15,6 +15,7 @@
 #include "hpcg_kernels.cuh"
 #include "hpcg_lines.cuh"
 #include "hpcg_tail.cuh"
+#include "hpcg_fixed.cuh"
 
 using namespace hpcg;
 
@@ -462,9 +463,17 @@ static int enqueue_zero(hpcg_ctx *h, int l, T *v, cudaStream_t s, const CgState 
 
 template <typename T, int NCH>
 static void launch_gs_lines(const LevelData &L, int count, int py, int pz, int pa, int steps, int vmask, const T *r, T *z, const T *invd,
-                            const CgState *st, const Inst *tabc, T *rc, const T *kap, cudaStream_t s) {
-  k_gs_lines<T, NCH><<<L.tab.nblk_line, dim3(32, L.tab.line_lpc), 0, s>>>(L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa,
-                                                                         steps, vmask, r, z, invd, st, tabc, rc, kap);
+                            const CgState *st, const Inst *tabc, T *rc, const T *kap, cudaStream_t s, bool fixed) {
+  const dim3 grid(L.tab.nblk_line), block(32, L.tab.line_lpc);
+  if constexpr (sizeof(T) == 8) {
+    if (fixed && NCH <= 6) {  // longer lines would spill registers: plain FP64 sums
+      k_gs_lines_fx<NCH><<<grid, block, 0, s>>>(L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa, steps, vmask, r, z, invd,
+                                                st, tabc, rc, kap);
+      return;
+    }
+  }
+  k_gs_lines<T, NCH><<<grid, block, 0, s>>>(L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa, steps, vmask, r, z, invd, st,
+                                            tabc, rc, kap);
 }
 
 // `steps` colour steps on the lines of class (py, pz), alternating x parity
@@ -480,7 +489,7 @@ static int enqueue_line_steps(hpcg_ctx *h, int l, int py, int pz, int pa, int st
   const Inst *tabc = rc ? h->lv[l + 1].tab.inst : nullptr;
   switch (L.tab.nch ? L.tab.nch2 : 0) {
 #define HPCG_GS_CASE(N) \
-  case N: launch_gs_lines<T, N>(L, h->count, py, pz, pa, steps, vmask, r, z, invd, st, tabc, rc, kap, s); break;
+  case N: launch_gs_lines<T, N>(L, h->count, py, pz, pa, steps, vmask, r, z, invd, st, tabc, rc, kap, s, h->opt.fixed_point != 0); break;
     HPCG_GS_CASE(1) HPCG_GS_CASE(2) HPCG_GS_CASE(3) HPCG_GS_CASE(4) HPCG_GS_CASE(5) HPCG_GS_CASE(6)
     HPCG_GS_CASE(8)
 #undef HPCG_GS_CASE
@@ -1003,6 +1012,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->check_every = 1;
   opt->max_rhs = 0;
   opt->autotune = 1;
+  opt->fixed_point = 1;
   opt->persistent = 0;
   return HPCG_OK;
 }

@@ -1,0 +1,294 @@
+// hpcg_fixed.cuh -- FP64 line kernels whose neighbour sums run on the integer
+// pipe in exact fixed point.
+//
+// On this GPU an FP64 add issues at 2 per SM per clock while 64-bit integer
+// adds issue at about 64 (128 32-bit ops).  The colour-pair and SpMV line
+// kernels spend most of their FP64 instructions summing neighbour values
+// whose coefficients are all 1 (the off-diagonal entries are -1).  Here every
+// value summed in one line-plane step is first mapped to a 64-bit integer
+// against a common exponent bound E of that step,
+//     q(v) = trunc(v * 2^(1080 - E)),  |v| < 2^(E - 1022)  =>  |q| < 2^58,
+// the sums are formed exactly in int64 (at most 27 terms: |sum| < 2^63), and
+// the result is converted back once (round to nearest, then an exact power-of-
+// two scale).  E is the largest biased exponent among the values of the step
+// (so |q| < 2^58 and 24 terms sum below 2^63); truncating each term costs at
+// most 2^-5 ulp of the largest value, so a 24-term sum is within one ulp of it:
+// tighter than the FP64 summation it replaces.  E is raised to at least 64, so
+// values below 2^-1016 in magnitude count as zero (an absolute error under
+// 1e-305); a warp whose step holds huge (E > 2000) or non-finite values
+// continues with FP64 sums, so NaN and Inf still propagate.  The colour-step
+// update itself (r + sum) / A_ii stays in FP64.
+#pragma once
+#include "hpcg_lines.cuh"
+
+namespace hpcg {
+
+constexpr int kFxMinE = 64, kFxMaxE = 2000;
+
+__device__ __forceinline__ int fx_exp(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
+
+// q(v) for a value whose biased exponent is at most E (E in [kFxMinE, kFxMaxE]).
+__device__ __forceinline__ long long fx_of(double v, int E) {
+  const int hi = __double2hiint(v);
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int e = (hi >> 20) & 0x7FF;
+  const unsigned long long m = ((unsigned long long)((unsigned)(hi & 0xFFFFF) | 0x100000u) << 32) | lo;
+  unsigned long long q;
+  // |v| = m 2^(e-1075); q = m 2^(e-E+5) = (m << 5) >> (E - e); shifts of 64 or
+  // more give 0 (zeros and denormals have e = 0 and E >= 64)
+  asm("shr.b64 %0, %1, %2;" : "=l"(q) : "l"(m << 5), "r"((unsigned)(E - e)));
+  const long long s = (long long)(hi >> 31);
+  return ((long long)q ^ s) - s;
+}
+
+// q 2^(E-1080) as FP64: one rounding (int64 -> double), then an exact scale.
+__device__ __forceinline__ double fx_to_double(long long q, int E) {
+  const double d = (double)q;
+  const long long bits = __double_as_longlong(d) + ((long long)(E - 1080) << 52);
+  return q == 0 ? 0.0 : __longlong_as_double(bits);
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+template <int NC>
+__device__ __forceinline__ void prev_of_i(const long long (&v)[NC], long long (&out)[NC], int lane) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const long long up = __shfl_up_sync(kFull, v[c], 1);
+    const long long last = __shfl_sync(kFull, v[c > 0 ? c - 1 : 0], 31);
+    out[c] = lane == 0 ? (c > 0 ? last : 0LL) : up;
+  }
+}
+template <int NC>
+__device__ __forceinline__ void next_of_i(const long long (&v)[NC], long long (&out)[NC], int lane) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const long long dn = __shfl_down_sync(kFull, v[c], 1);
+    const long long first = __shfl_sync(kFull, v[c + 1 < NC ? c + 1 : c], 0);
+    out[c] = lane == 31 ? (c + 1 < NC ? first : 0LL) : dn;
+  }
+}
+
+// Raw values of one x-line (parity split), zero where absent or invalid.
+template <int NC>
+__device__ __forceinline__ void load_line(const double *__restrict__ line, bool ok, int nx, int lane, double (&e)[NC], double (&o)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+    e[c] = (ok && xe < nx) ? __ldg(line + xe) : 0.0;
+    o[c] = (ok && xo < nx) ? __ldg(line + xo) : 0.0;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ int max_exp3(const double (&a)[NC], const double (&b)[NC], int m) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m = max(m, max(fx_exp(a[c]), fx_exp(b[c])));
+  return m;
+}
+
+// Colour steps along the own line (FP64), the stores, and the fused
+// residual + injection: the part of k_gs_lines after the off-line sums.
+template <int NC>
+__device__ __forceinline__ void pair_update(const Inst &g, int ii, int zz, int y, int lane, int pa, int steps, bool own_valid,
+                                            const double (&PE)[NC], const double (&PO)[NC], const double *__restrict__ rg,
+                                            double *__restrict__ zg, const double *__restrict__ invd, const Inst *__restrict__ tabc,
+                                            double *__restrict__ rc, const double *__restrict__ kap) {
+  const int nx = g.nx;
+  const long rowbase = (long)zz * nx * g.ny + (long)y * nx;
+  double E_[NC], O_[NC], rE[NC], rO[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+    E_[c] = (xe < nx && own_valid) ? zg[rowbase + xe] : 0.0;
+    O_[c] = (xo < nx && own_valid) ? zg[rowbase + xo] : 0.0;
+    rE[c] = xe < nx ? rg[rowbase + xe] : 0.0;
+    rO[c] = xo < nx ? rg[rowbase + xo] : 0.0;
+  }
+  double nb[NC];
+  for (int s = 0; s < steps; ++s) {
+    const int q = (s & 1) ? 1 - pa : pa;
+    if (q == 0) {
+      prev_of<double, NC>(O_, nb, lane);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 2 * (lane + 32 * c);
+        if (xe < nx) {
+          const double id = invd ? invd[g.off + rowbase + xe] : 1.0 / 26.0;
+          E_[c] = (((rE[c] + PE[c]) + nb[c]) + O_[c]) * id;
+        }
+      }
+    } else {
+      next_of<double, NC>(E_, nb, lane);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int xo = 2 * (lane + 32 * c) + 1;
+        if (xo < nx) {
+          const double id = invd ? invd[g.off + rowbase + xo] : 1.0 / 26.0;
+          O_[c] = (((rO[c] + PO[c]) + E_[c]) + nb[c]) * id;
+        }
+      }
+    }
+  }
+  const bool write_e = steps > 1 || !own_valid || pa == 0;
+  const bool write_o = steps > 1 || !own_valid || pa == 1;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+    if (write_e && xe < nx) zg[rowbase + xe] = E_[c];
+    if (write_o && xo < nx) zg[rowbase + xo] = O_[c];
+  }
+  if (rc) {
+    const Inst gc = tabc[ii];
+    const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int xe = 2 * (lane + 32 * c);
+      if (xe < nx) {
+        const double d = kap ? 26.0 + kap[g.off + rowbase + xe] : 26.0;
+        const double nbs = (PE[c] + nb[c]) + O_[c];
+        rc[cbase + (xe >> 1)] = rE[c] - (d * E_[c] - nbs);
+      }
+    }
+  }
+}
+
+// Colour-pair kernel (see k_gs_lines) with the off-line sums in fixed point.
+template <int NC>
+__global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
+                                                     int steps, int vmask, const double *__restrict__ r, double *__restrict__ z,
+                                                     const double *__restrict__ invd, const CgState *__restrict__ st,
+                                                     const Inst *__restrict__ tabc, double *__restrict__ rc,
+                                                     const double *__restrict__ kap) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<4>(tab, count, blk);
+  const Inst g = tab[ii];
+  if (st && st[ii].done) return;
+  const int cy = (g.ny - py + 1) / 2, cz = (g.nz - pz + 1) / 2;
+  const int nby = (half_up(g.ny) + lpc - 1) / lpc;
+  const int lb = blk - g.blk_line;
+  const int j = (lb % nby) * lpc + threadIdx.y;
+  const int m0 = (lb / nby) * zc;
+  const int m1 = min(m0 + zc, cz);
+  if (j >= cy || m0 >= m1) return;  // whole warp
+  const int lane = threadIdx.x;
+  const int y = 2 * j + py;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long sxy = (long)nx * ny;
+  double *zg = z + g.off;
+  const double *rg = r + g.off;
+  const bool vy = (vmask >> line_class(y + 1, pz)) & 1;       // lines (y +- 1, z) of the updated planes
+  const bool ym = y - 1 >= 0 && vy, yp = y + 1 < ny && vy;
+  const bool own_valid = (vmask >> line_class(y, pz)) & 1;
+  const bool vyo = (vmask >> line_class(y + 1, pz + 1)) & 1;  // lines (y +- 1, z +- 1)
+  const bool vy0 = (vmask >> line_class(y, pz + 1)) & 1;      // line (y, z +- 1)
+
+  int m = m0;
+  int Ep = kFxMinE;
+  long long tpe[NC], tpo[NC];  // fixed-point plane sums of the plane below the current one
+  bool fixed = true;
+  {
+    const int zz = 2 * m0 + pz - 1;
+    const bool zin = zz >= 0;
+    double ae[NC], ao[NC], be[NC], bo[NC], de[NC], d_o[NC];
+    const double *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
+    load_line<NC>(lm, zin && y - 1 >= 0 && vyo, nx, lane, ae, ao);
+    load_line<NC>(lm + nx, zin && vy0, nx, lane, be, bo);
+    load_line<NC>(lm + 2 * nx, zin && y + 1 < ny && vyo, nx, lane, de, d_o);
+    Ep = max(warp_max(max_exp3<NC>(ae, ao, max_exp3<NC>(be, bo, max_exp3<NC>(de, d_o, 0)))), kFxMinE);
+    fixed = Ep <= kFxMaxE;
+    if (fixed) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        tpe[c] = (fx_of(ae[c], Ep) + fx_of(be[c], Ep)) + fx_of(de[c], Ep);
+        tpo[c] = (fx_of(ao[c], Ep) + fx_of(bo[c], Ep)) + fx_of(d_o[c], Ep);
+      }
+    }
+  }
+  double tdpe[NC], tdpo[NC];  // FP64 plane sums once a warp has left the fixed point
+  if (fixed) {
+    for (; m < m1; ++m) {
+      const int zz = 2 * m + pz;
+      const bool zin = zz + 1 < nz;
+      double ae[NC], ao[NC], be[NC], bo[NC], de[NC], d_o[NC], ue[NC], uo[NC], we[NC], wo[NC];
+      const double *lm = zg + (long)(zz + 1) * sxy + (long)(y - 1) * nx;
+      load_line<NC>(lm, zin && y - 1 >= 0 && vyo, nx, lane, ae, ao);
+      load_line<NC>(lm + nx, zin && vy0, nx, lane, be, bo);
+      load_line<NC>(lm + 2 * nx, zin && y + 1 < ny && vyo, nx, lane, de, d_o);
+      const double *vm = zg + (long)zz * sxy + (long)(y - 1) * nx;
+      load_line<NC>(vm, ym, nx, lane, ue, uo);
+      load_line<NC>(vm + 2 * nx, yp, nx, lane, we, wo);
+      const int E = max(warp_max(max_exp3<NC>(ae, ao, max_exp3<NC>(be, bo, max_exp3<NC>(de, d_o,
+                                                                  max_exp3<NC>(ue, uo, max_exp3<NC>(we, wo, 0)))))),
+                        Ep);
+      if (E > kFxMaxE) {  // huge or non-finite values: FP64 from here on
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          tdpe[c] = fx_to_double(tpe[c], Ep);
+          tdpo[c] = fx_to_double(tpo[c], Ep);
+        }
+        fixed = false;
+        break;
+      }
+      long long ce[NC], co[NC], sh[NC];
+      const unsigned ds = (unsigned)(E - Ep);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const long long pe = ds < 64 ? tpe[c] >> ds : (tpe[c] < 0 ? -1LL : 0LL);  // earlier plane sums to the new scale
+        const long long po = ds < 64 ? tpo[c] >> ds : (tpo[c] < 0 ? -1LL : 0LL);
+        const long long te = (fx_of(ae[c], E) + fx_of(be[c], E)) + fx_of(de[c], E);
+        const long long to = (fx_of(ao[c], E) + fx_of(bo[c], E)) + fx_of(d_o[c], E);
+        ce[c] = (pe + te) + (fx_of(ue[c], E) + fx_of(we[c], E));  // off-line column sums at x
+        co[c] = (po + to) + (fx_of(uo[c], E) + fx_of(wo[c], E));
+        tpe[c] = te;
+        tpo[c] = to;
+      }
+      Ep = E;
+      double PE[NC], PO[NC];
+      prev_of_i<NC>(co, sh, lane);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) PE[c] = fx_to_double((sh[c] + ce[c]) + co[c], E);
+      next_of_i<NC>(ce, sh, lane);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) PO[c] = fx_to_double((ce[c] + co[c]) + sh[c], E);
+      pair_update<NC>(g, ii, zz, y, lane, pa, steps, own_valid, PE, PO, rg, zg, invd, tabc, rc, kap);
+    }
+  } else {
+    tsum2<double, NC, false>(zg, nx, ny, nz, y, 2 * m0 + pz - 1, lane, tdpe, tdpo, vmask);
+  }
+  // FP64 sums for the remaining planes (rare: huge or non-finite values)
+  for (; m < m1; ++m) {
+    const int zz = 2 * m + pz;
+    double tne[NC], tno[NC], PE[NC], PO[NC], ce[NC], co[NC], sh[NC];
+    tsum2<double, NC, false>(zg, nx, ny, nz, y, zz + 1, lane, tne, tno, vmask);
+    const double *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
+    const double *lp = lm + 2 * nx;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+      double ve = 0.0, vo = 0.0;
+      if (xe < nx) ve = (ym ? __ldg(lm + xe) : 0.0) + (yp ? __ldg(lp + xe) : 0.0);
+      if (xo < nx) vo = (ym ? __ldg(lm + xo) : 0.0) + (yp ? __ldg(lp + xo) : 0.0);
+      ce[c] = (tdpe[c] + tne[c]) + ve;
+      co[c] = (tdpo[c] + tno[c]) + vo;
+    }
+    prev_of<double, NC>(co, sh, lane);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) PE[c] = (sh[c] + ce[c]) + co[c];
+    next_of<double, NC>(ce, sh, lane);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) PO[c] = (ce[c] + co[c]) + sh[c];
+    pair_update<NC>(g, ii, zz, y, lane, pa, steps, own_valid, PE, PO, rg, zg, invd, tabc, rc, kap);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      tdpe[c] = tne[c];
+      tdpo[c] = tno[c];
+    }
+  }
+}
+
+}  // namespace hpcg
