@@ -374,9 +374,12 @@ def run_gpu(args):
     k1.record(stream)
     torch.cuda.synchronize()
     sp_ms = k0.elapsed_time(k1) / reps
-    spmv = {"kernel": "k_spmv_lines<double>", "ms": sp_ms, "fp64_instr_per_row": 7 + 4.0 / zr,
-            "g_fp64_instr_s": n * (7 + 4.0 / zr) / (sp_ms * 1e-3) / 1e9,
-            "hbm_gbs_algorithmic": 16 * n / (sp_ms * 1e-3) / 1e9}
+    # k_spmv_lines_fx: the 27-point box sum in fixed point; FP64 per row = its
+    # conversion + one FMA (27 x - S)
+    spmv = {"kernel": "k_spmv_lines_fx<6,0>", "ms": sp_ms, "fp64_instr_per_row": 2,
+            "g_fp64_instr_s": n * 2 / (sp_ms * 1e-3) / 1e9,
+            "hbm_gbs_algorithmic": 16 * n / (sp_ms * 1e-3) / 1e9,
+            "hbm_frac_of_measured": 16 * n / (sp_ms * 1e-3) / 1e9 / measured_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS)}
     del xs_, ys_
 
     # --- mixed vs FP64 time to 1e-9 (b = A x_true, x_true ~ U[-1,1], seed 1)

@@ -550,16 +550,28 @@ static int enqueue_smoother(hpcg_ctx *h, int l, const T *r, T *z, int sweeps, cu
 
 // y = A x (Mode 0) or y = b - A x (Mode 1) on level l; optional p.Ap partials
 // (then finalize with stencil mode 2).
+template <typename T, int N, int Mode>
+static void launch_spmv_lines(hpcg_ctx *h, const LevelData &L, const T *x, const T *b, T *y, const T *kap, double *partials,
+                              const CgState *st, cudaStream_t s) {
+  const dim3 blk(32, L.tab.row_lpc);
+  if constexpr (sizeof(T) == 8 && N <= 8) {
+    if (h->opt.fixed_point) {
+      k_spmv_lines_fx<N, Mode><<<L.tab.nblk_row, blk, 0, s>>>(L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, partials,
+                                                              st);
+      return;
+    }
+  }
+  k_spmv_lines<T, N, Mode><<<L.tab.nblk_row, blk, 0, s>>>(L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, partials, st);
+}
+
 template <typename T, int Mode>
 static int enqueue_spmv(hpcg_ctx *h, int l, const T *x, const T *b, T *y, const T *kap, double *partials, const CgState *st,
                         cudaStream_t s) {
   const LevelData &L = h->lv[l];
-  const dim3 blk(32, L.tab.row_lpc);
   switch (L.tab.nch) {
-#define HPCG_SP_CASE(N)                                                                                                          \
-  case N:                                                                                                                        \
-    k_spmv_lines<T, N, Mode><<<L.tab.nblk_row, blk, 0, s>>>(L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, \
-                                                            partials, st);                                                     \
+#define HPCG_SP_CASE(N)                                                          \
+  case N:                                                                        \
+    launch_spmv_lines<T, N, Mode>(h, L, x, b, y, kap, partials, st, s);          \
     break;
     HPCG_SP_CASE(1) HPCG_SP_CASE(2) HPCG_SP_CASE(3) HPCG_SP_CASE(4) HPCG_SP_CASE(5) HPCG_SP_CASE(6)
     HPCG_SP_CASE(7) HPCG_SP_CASE(8) HPCG_SP_CASE(10) HPCG_SP_CASE(12) HPCG_SP_CASE(16)

@@ -291,4 +291,161 @@ __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ ta
   }
 }
 
+// Raw values of one x-line, x = lane + 32c (SpMV layout), zero where absent.
+template <int NC>
+__device__ __forceinline__ void load_row(const double *__restrict__ line, bool ok, int nx, int lane, double (&v)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int x = lane + 32 * c;
+    v[c] = (ok && x < nx) ? __ldg(line + x) : 0.0;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ int max_exp_row(const double (&a)[NC], int m) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m = max(m, fx_exp(a[c]));
+  return m;
+}
+
+template <int NC>
+__device__ __forceinline__ void line_neighbours_i(const long long (&v)[NC], long long (&vl)[NC], long long (&vr)[NC], int lane) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const long long up = __shfl_up_sync(kFull, v[c], 1);
+    const long long prev_last = __shfl_sync(kFull, v[c > 0 ? c - 1 : 0], 31);
+    vl[c] = lane == 0 ? (c > 0 ? prev_last : 0LL) : up;
+    const long long dn = __shfl_down_sync(kFull, v[c], 1);
+    const long long next_first = __shfl_sync(kFull, v[c + 1 < NC ? c + 1 : c], 0);
+    vr[c] = lane == 31 ? (c + 1 < NC ? next_first : 0LL) : dn;
+  }
+}
+
+// y = A x (Mode 0) or y = b - A x (Mode 1) over every x-line (see
+// k_spmv_lines): A x = (27 + kappa) x - S with the 27-point box sum S formed
+// exactly in fixed point (plane sums over y, then over z, then over x).
+template <int NC, int Mode>
+__global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ tab, int count, int lpc, int zc, const double *__restrict__ x,
+                                                       const double *__restrict__ b, double *__restrict__ y, const double *__restrict__ kap,
+                                                       double *__restrict__ partials, const CgState *__restrict__ st) {
+  const int blk = blockIdx.x;
+  const int ii = find_inst<3>(tab, count, blk);
+  const Inst g = tab[ii];
+  const bool skip = st && st[ii].done;
+  const int nby = (g.ny + lpc - 1) / lpc;
+  const int lb = blk - g.blk_row;
+  const int yy = (lb % nby) * lpc + threadIdx.y;
+  const int z0 = (lb / nby) * zc;
+  const int z1 = min(z0 + zc, g.nz);
+  const int lane = threadIdx.x;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long sxy = (long)nx * ny;
+  const double *xg = x + g.off;
+  if (skip) {
+    if (partials && yy < ny && lane == 0)
+      for (int zz = z0; zz < z1; ++zz) partials[g.poff + (long)zz * ny + yy] = 0.0;
+    return;
+  }
+  if (yy >= ny || z0 >= z1) return;
+  const bool ym = yy - 1 >= 0, yp = yy + 1 < ny;
+  // plane sums over y-1..y+1 of planes z0-1 and z0, fixed point at scale Ep
+  long long t0[NC], t1[NC];
+  double d0[NC], d1[NC];  // the same in FP64 once a warp leaves the fixed point
+  int Ep;
+  bool fixed;
+  {
+    double am[NC], a0[NC], ap[NC], bm[NC], b0[NC], bp[NC];
+    const double *l = xg + (long)(z0 - 1) * sxy + (long)(yy - 1) * nx;
+    load_row<NC>(l, z0 - 1 >= 0 && ym, nx, lane, am);
+    load_row<NC>(l + nx, z0 - 1 >= 0, nx, lane, a0);
+    load_row<NC>(l + 2 * nx, z0 - 1 >= 0 && yp, nx, lane, ap);
+    load_row<NC>(l + sxy, ym, nx, lane, bm);
+    load_row<NC>(l + sxy + nx, true, nx, lane, b0);
+    load_row<NC>(l + sxy + 2 * nx, yp, nx, lane, bp);
+    int E = max_exp_row<NC>(am, max_exp_row<NC>(a0, max_exp_row<NC>(ap, 0)));
+    E = max_exp_row<NC>(bm, max_exp_row<NC>(b0, max_exp_row<NC>(bp, E)));
+    Ep = max(warp_max(E), kFxMinE);
+    fixed = Ep <= kFxMaxE;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (fixed) {
+        t0[c] = (fx_of(am[c], Ep) + fx_of(a0[c], Ep)) + fx_of(ap[c], Ep);
+        t1[c] = (fx_of(bm[c], Ep) + fx_of(b0[c], Ep)) + fx_of(bp[c], Ep);
+      } else {
+        d0[c] = (am[c] + a0[c]) + ap[c];
+        d1[c] = (bm[c] + b0[c]) + bp[c];
+      }
+    }
+  }
+  for (int zz = z0; zz < z1; ++zz) {
+    double cm[NC], c0[NC], cp[NC];
+    const double *l = xg + (long)(zz + 1) * sxy + (long)(yy - 1) * nx;
+    const bool zin = zz + 1 < nz;
+    load_row<NC>(l, zin && ym, nx, lane, cm);
+    load_row<NC>(l + nx, zin, nx, lane, c0);
+    load_row<NC>(l + 2 * nx, zin && yp, nx, lane, cp);
+    double S[NC];
+    if (fixed) {
+      const int E = max(warp_max(max_exp_row<NC>(cm, max_exp_row<NC>(c0, max_exp_row<NC>(cp, 0)))), Ep);
+      if (E > kFxMaxE) {  // huge or non-finite values: FP64 from here on
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          d0[c] = fx_to_double(t0[c], Ep);
+          d1[c] = fx_to_double(t1[c], Ep);
+        }
+        fixed = false;
+      } else {
+        const unsigned ds = (unsigned)(E - Ep);
+        long long u[NC], ul[NC], ur[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const long long a = ds < 64 ? t0[c] >> ds : (t0[c] < 0 ? -1LL : 0LL);
+          const long long bb = ds < 64 ? t1[c] >> ds : (t1[c] < 0 ? -1LL : 0LL);
+          const long long t2 = (fx_of(cm[c], E) + fx_of(c0[c], E)) + fx_of(cp[c], E);
+          u[c] = (a + bb) + t2;
+          t0[c] = bb;
+          t1[c] = t2;
+        }
+        Ep = E;
+        line_neighbours_i<NC>(u, ul, ur, lane);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) S[c] = fx_to_double((ul[c] + u[c]) + ur[c], E);
+      }
+    }
+    if (!fixed) {
+      double u[NC], ul[NC], ur[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double t2 = (cm[c] + c0[c]) + cp[c];
+        u[c] = (d0[c] + d1[c]) + t2;
+        d0[c] = d1[c];
+        d1[c] = t2;
+      }
+      line_neighbours<double, NC>(u, ul, ur, lane);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) S[c] = (ul[c] + u[c]) + ur[c];
+    }
+    const long rowbase = (long)zz * sxy + (long)yy * nx;
+    double dotv = 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int xx = lane + 32 * c;
+      if (xx < nx) {
+        const double xi = xg[rowbase + xx];
+        const long gi = g.off + rowbase + xx;
+        const double d1 = kap ? 27.0 + kap[gi] : 27.0;
+        const double ax = d1 * xi - S[c];
+        const double out = Mode == 0 ? ax : b[gi] - ax;
+        y[gi] = out;
+        if (partials) dotv += xi * out;
+      }
+    }
+    if (partials) {  // fixed shuffle tree over the lanes of this line
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dotv += __shfl_down_sync(kFull, dotv, o);
+      if (lane == 0) partials[g.poff + (long)zz * ny + yy] = dotv;
+    }
+  }
+}
+
 }  // namespace hpcg
