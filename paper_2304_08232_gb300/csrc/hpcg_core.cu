@@ -683,7 +683,7 @@ static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_ite
   TRY((enqueue_spmv<double, 1>(h, 0, x, b, h->cg_r, h->has_kappa ? L0.kap : nullptr, nullptr, nullptr, s)));
   k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_r, h->part, h->st);
   CKL("k_dot_partial");
-  k_finalize<FIN_NORM0><<<h->count, kFinThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  k_finalize<FIN_NORM0><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<NORM0>");
   if (max_iters <= 0) {
     // nothing to iterate: mark every instance done
@@ -701,7 +701,7 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st));  // z = M r
   k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_z, h->part, h->st);
   CKL("k_dot_partial");
-  k_finalize<FIN_RTZ><<<h->count, kFinThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  k_finalize<FIN_RTZ><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<RTZ>");
   k_update_p<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_z, h->cg_p, h->st);  // p = z + beta p
   CKL("k_update_p");
@@ -710,7 +710,7 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   CKL("k_finalize<PAP>");
   k_update_xr<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r, h->part, h->st);
   CKL("k_update_xr");
-  k_finalize<FIN_NORM><<<h->count, kFinThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  k_finalize<FIN_NORM><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<NORM>");
   return HPCG_OK;
 }

@@ -84,6 +84,15 @@ __device__ __forceinline__ void load_line(const double *__restrict__ line, bool 
   }
 }
 
+// A read-only load the compiler may not merge with an earlier one: the
+// fixed-point kernels read each value twice (exponent pass, conversion pass)
+// rather than keep it in a register between the passes.
+__device__ __forceinline__ double ld_nc_again(const double *p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
 template <int NC>
 __device__ __forceinline__ int max_exp3(const double (&a)[NC], const double (&b)[NC], int m) {
 #pragma unroll
@@ -301,6 +310,27 @@ __device__ __forceinline__ void load_row(const double *__restrict__ line, bool o
   }
 }
 
+// Row layout (x = lane + 32c) versions of the two passes.
+template <int NC>
+__device__ __forceinline__ int row_max_exp(const double *__restrict__ line, bool ok, int nx, int lane, int m) {
+  if (!ok) return m;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int x = lane + 32 * c;
+    if (x < nx) m = max(m, fx_exp(ld_nc_again(line + x)));
+  }
+  return m;
+}
+template <int NC>
+__device__ __forceinline__ void row_add_fx(const double *__restrict__ line, bool ok, int nx, int lane, int E, long long (&acc)[NC]) {
+  if (!ok) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int x = lane + 32 * c;
+    if (x < nx) acc[c] += fx_of(ld_nc_again(line + x), E);
+  }
+}
+
 template <int NC>
 __device__ __forceinline__ int max_exp_row(const double (&a)[NC], int m) {
 #pragma unroll
@@ -354,39 +384,39 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
   int Ep;
   bool fixed;
   {
-    double am[NC], a0[NC], ap[NC], bm[NC], b0[NC], bp[NC];
     const double *l = xg + (long)(z0 - 1) * sxy + (long)(yy - 1) * nx;
-    load_row<NC>(l, z0 - 1 >= 0 && ym, nx, lane, am);
-    load_row<NC>(l + nx, z0 - 1 >= 0, nx, lane, a0);
-    load_row<NC>(l + 2 * nx, z0 - 1 >= 0 && yp, nx, lane, ap);
-    load_row<NC>(l + sxy, ym, nx, lane, bm);
-    load_row<NC>(l + sxy + nx, true, nx, lane, b0);
-    load_row<NC>(l + sxy + 2 * nx, yp, nx, lane, bp);
-    int E = max_exp_row<NC>(am, max_exp_row<NC>(a0, max_exp_row<NC>(ap, 0)));
-    E = max_exp_row<NC>(bm, max_exp_row<NC>(b0, max_exp_row<NC>(bp, E)));
-    Ep = max(warp_max(E), kFxMinE);
+    const bool za = z0 - 1 >= 0;
+    int e = row_max_exp<NC>(l, za && ym, nx, lane, 0);
+    e = row_max_exp<NC>(l + nx, za, nx, lane, e);
+    e = row_max_exp<NC>(l + 2 * nx, za && yp, nx, lane, e);
+    e = row_max_exp<NC>(l + sxy, ym, nx, lane, e);
+    e = row_max_exp<NC>(l + sxy + nx, true, nx, lane, e);
+    e = row_max_exp<NC>(l + sxy + 2 * nx, yp, nx, lane, e);
+    Ep = max(warp_max(e), kFxMinE);
     fixed = Ep <= kFxMaxE;
+    if (fixed) {
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (fixed) {
-        t0[c] = (fx_of(am[c], Ep) + fx_of(a0[c], Ep)) + fx_of(ap[c], Ep);
-        t1[c] = (fx_of(bm[c], Ep) + fx_of(b0[c], Ep)) + fx_of(bp[c], Ep);
-      } else {
-        d0[c] = (am[c] + a0[c]) + ap[c];
-        d1[c] = (bm[c] + b0[c]) + bp[c];
-      }
+      for (int c = 0; c < NC; ++c) t0[c] = t1[c] = 0;
+      row_add_fx<NC>(l, za && ym, nx, lane, Ep, t0);
+      row_add_fx<NC>(l + nx, za, nx, lane, Ep, t0);
+      row_add_fx<NC>(l + 2 * nx, za && yp, nx, lane, Ep, t0);
+      row_add_fx<NC>(l + sxy, ym, nx, lane, Ep, t1);
+      row_add_fx<NC>(l + sxy + nx, true, nx, lane, Ep, t1);
+      row_add_fx<NC>(l + sxy + 2 * nx, yp, nx, lane, Ep, t1);
+    } else {
+      tsum<double, NC>(xg, nx, ny, nz, yy, z0 - 1, lane, d0);
+      tsum<double, NC>(xg, nx, ny, nz, yy, z0, lane, d1);
     }
   }
   for (int zz = z0; zz < z1; ++zz) {
-    double cm[NC], c0[NC], cp[NC];
     const double *l = xg + (long)(zz + 1) * sxy + (long)(yy - 1) * nx;
     const bool zin = zz + 1 < nz;
-    load_row<NC>(l, zin && ym, nx, lane, cm);
-    load_row<NC>(l + nx, zin, nx, lane, c0);
-    load_row<NC>(l + 2 * nx, zin && yp, nx, lane, cp);
     double S[NC];
     if (fixed) {
-      const int E = max(warp_max(max_exp_row<NC>(cm, max_exp_row<NC>(c0, max_exp_row<NC>(cp, 0)))), Ep);
+      int e = row_max_exp<NC>(l, zin && ym, nx, lane, 0);
+      e = row_max_exp<NC>(l + nx, zin, nx, lane, e);
+      e = row_max_exp<NC>(l + 2 * nx, zin && yp, nx, lane, e);
+      const int E = max(warp_max(e), Ep);
       if (E > kFxMaxE) {  // huge or non-finite values: FP64 from here on
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -396,15 +426,22 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
         fixed = false;
       } else {
         const unsigned ds = (unsigned)(E - Ep);
-        long long u[NC], ul[NC], ur[NC];
+        long long u[NC], t2[NC], ul[NC], ur[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const long long a = ds < 64 ? t0[c] >> ds : (t0[c] < 0 ? -1LL : 0LL);
           const long long bb = ds < 64 ? t1[c] >> ds : (t1[c] < 0 ? -1LL : 0LL);
-          const long long t2 = (fx_of(cm[c], E) + fx_of(c0[c], E)) + fx_of(cp[c], E);
-          u[c] = (a + bb) + t2;
+          u[c] = a + bb;
           t0[c] = bb;
-          t1[c] = t2;
+          t2[c] = 0;
+        }
+        row_add_fx<NC>(l, zin && ym, nx, lane, E, t2);
+        row_add_fx<NC>(l + nx, zin, nx, lane, E, t2);
+        row_add_fx<NC>(l + 2 * nx, zin && yp, nx, lane, E, t2);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          u[c] += t2[c];
+          t1[c] = t2[c];
         }
         Ep = E;
         line_neighbours_i<NC>(u, ul, ur, lane);
@@ -413,13 +450,13 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
       }
     }
     if (!fixed) {
-      double u[NC], ul[NC], ur[NC];
+      double t2[NC], u[NC], ul[NC], ur[NC];
+      tsum<double, NC>(xg, nx, ny, nz, yy, zz + 1, lane, t2);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const double t2 = (cm[c] + c0[c]) + cp[c];
-        u[c] = (d0[c] + d1[c]) + t2;
+        u[c] = (d0[c] + d1[c]) + t2[c];
         d0[c] = d1[c];
-        d1[c] = t2;
+        d1[c] = t2[c];
       }
       line_neighbours<double, NC>(u, ul, ur, lane);
 #pragma unroll

@@ -214,6 +214,8 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const Inst *__restr
 //  FIN_OUT:   out[inst] = sum               (plain dot product)
 // `stencil` selects the stencil blocking (partials written by k_spmv) instead
 // of the reduction blocking.
+// Launched with kFinThreads threads for the per-line partials of the SpMV
+// (tens of thousands) and kRedThreads for the reduction partials (hundreds).
 template <int Kind>
 __global__ void __launch_bounds__(kFinThreads) k_finalize(const Inst *__restrict__ tab, int count, const double *__restrict__ partials,
                                                           int stencil, CgState *__restrict__ st, double *__restrict__ hist,
