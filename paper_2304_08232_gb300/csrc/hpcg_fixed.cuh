@@ -166,7 +166,33 @@ __device__ __forceinline__ void pair_update(const Inst &g, int ii, int zz, int y
   }
 }
 
+// Arithmetic right shift that saturates for shifts of 64 or more.
+__device__ __forceinline__ long long shr_fx(long long v, int d) { return d < 64 ? v >> d : (v < 0 ? -1LL : 0LL); }
+
+template <int NC>
+__device__ __forceinline__ void prev_of_int(const int (&v)[NC], int (&out)[NC], int lane) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int up = __shfl_up_sync(kFull, v[c], 1);
+    const int last = __shfl_sync(kFull, v[c > 0 ? c - 1 : 0], 31);
+    out[c] = lane == 0 ? (c > 0 ? last : v[c]) : up;
+  }
+}
+template <int NC>
+__device__ __forceinline__ void next_of_int(const int (&v)[NC], int (&out)[NC], int lane) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int dn = __shfl_down_sync(kFull, v[c], 1);
+    const int first = __shfl_sync(kFull, v[c + 1 < NC ? c + 1 : c], 0);
+    out[c] = lane == 31 ? (c + 1 < NC ? first : v[c]) : dn;
+  }
+}
+
 // Colour-pair kernel (see k_gs_lines) with the off-line sums in fixed point.
+// Every lane scales each of its 32-wide chunks (the x pair 2k, 2k+1) by that
+// chunk's own exponent bound, so only one chunk's raw values are live at a
+// time; the x-window sum aligns the three columns it adds to their largest
+// bound.  Bounds only grow along z within a block's planes.
 template <int NC>
 __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
                                                      int steps, int vmask, const double *__restrict__ r, double *__restrict__ z,
@@ -197,105 +223,124 @@ __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ ta
   const bool vy0 = (vmask >> line_class(y, pz + 1)) & 1;      // line (y, z +- 1)
 
   int m = m0;
-  int Ep = kFxMinE;
   long long tpe[NC], tpo[NC];  // fixed-point plane sums of the plane below the current one
-  bool fixed = true;
+  int Ec[NC];                  // their per-chunk scale
+  bool fixed;
   {
     const int zz = 2 * m0 + pz - 1;
     const bool zin = zz >= 0;
-    double ae[NC], ao[NC], be[NC], bo[NC], de[NC], d_o[NC];
-    const double *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
-    load_line<NC>(lm, zin && y - 1 >= 0 && vyo, nx, lane, ae, ao);
-    load_line<NC>(lm + nx, zin && vy0, nx, lane, be, bo);
-    load_line<NC>(lm + 2 * nx, zin && y + 1 < ny && vyo, nx, lane, de, d_o);
-    Ep = max(warp_max(max_exp3<NC>(ae, ao, max_exp3<NC>(be, bo, max_exp3<NC>(de, d_o, 0)))), kFxMinE);
-    fixed = Ep <= kFxMaxE;
-    if (fixed) {
+    const double *la = zg + (long)zz * sxy + (long)(y - 1) * nx;
+    const bool oka = zin && y - 1 >= 0 && vyo, okb = zin && vy0, okd = zin && y + 1 < ny && vyo;
+    bool bad = false;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        tpe[c] = (fx_of(ae[c], Ep) + fx_of(be[c], Ep)) + fx_of(de[c], Ep);
-        tpo[c] = (fx_of(ao[c], Ep) + fx_of(bo[c], Ep)) + fx_of(d_o[c], Ep);
-      }
+    for (int c = 0; c < NC; ++c) {
+      const int xe = 64 * c + 2 * lane, xo = xe + 1;
+      const bool ie = xe < nx, io = xo < nx;
+      const double ae = (oka && ie) ? __ldg(la + xe) : 0.0, ao = (oka && io) ? __ldg(la + xo) : 0.0;
+      const double be = (okb && ie) ? __ldg(la + nx + xe) : 0.0, bo = (okb && io) ? __ldg(la + nx + xo) : 0.0;
+      const double de = (okd && ie) ? __ldg(la + 2 * nx + xe) : 0.0, d_o = (okd && io) ? __ldg(la + 2 * nx + xo) : 0.0;
+      const int e = max(max(max(fx_exp(ae), fx_exp(ao)), max(fx_exp(be), fx_exp(bo))), max(max(fx_exp(de), fx_exp(d_o)), kFxMinE));
+      bad |= e > kFxMaxE;
+      Ec[c] = e;
+      tpe[c] = (fx_of(ae, e) + fx_of(be, e)) + fx_of(de, e);
+      tpo[c] = (fx_of(ao, e) + fx_of(bo, e)) + fx_of(d_o, e);
     }
+    fixed = !__any_sync(kFull, bad);
   }
-  double tdpe[NC], tdpo[NC];  // FP64 plane sums once a warp has left the fixed point
   if (fixed) {
     for (; m < m1; ++m) {
       const int zz = 2 * m + pz;
       const bool zin = zz + 1 < nz;
-      double ae[NC], ao[NC], be[NC], bo[NC], de[NC], d_o[NC], ue[NC], uo[NC], we[NC], wo[NC];
-      const double *lm = zg + (long)(zz + 1) * sxy + (long)(y - 1) * nx;
-      load_line<NC>(lm, zin && y - 1 >= 0 && vyo, nx, lane, ae, ao);
-      load_line<NC>(lm + nx, zin && vy0, nx, lane, be, bo);
-      load_line<NC>(lm + 2 * nx, zin && y + 1 < ny && vyo, nx, lane, de, d_o);
+      const double *la = zg + (long)(zz + 1) * sxy + (long)(y - 1) * nx;
       const double *vm = zg + (long)zz * sxy + (long)(y - 1) * nx;
-      load_line<NC>(vm, ym, nx, lane, ue, uo);
-      load_line<NC>(vm + 2 * nx, yp, nx, lane, we, wo);
-      const int E = max(warp_max(max_exp3<NC>(ae, ao, max_exp3<NC>(be, bo, max_exp3<NC>(de, d_o,
-                                                                  max_exp3<NC>(ue, uo, max_exp3<NC>(we, wo, 0)))))),
-                        Ep);
-      if (E > kFxMaxE) {  // huge or non-finite values: FP64 from here on
+      const bool oka = zin && y - 1 >= 0 && vyo, okb = zin && vy0, okd = zin && y + 1 < ny && vyo;
+      long long ce[NC], co[NC], nte[NC], nto[NC];
+      int En[NC];
+      bool bad = false;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          tdpe[c] = fx_to_double(tpe[c], Ep);
-          tdpo[c] = fx_to_double(tpo[c], Ep);
-        }
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 64 * c + 2 * lane, xo = xe + 1;
+        const bool ie = xe < nx, io = xo < nx;
+        const double ae = (oka && ie) ? __ldg(la + xe) : 0.0, ao = (oka && io) ? __ldg(la + xo) : 0.0;
+        const double be = (okb && ie) ? __ldg(la + nx + xe) : 0.0, bo = (okb && io) ? __ldg(la + nx + xo) : 0.0;
+        const double de = (okd && ie) ? __ldg(la + 2 * nx + xe) : 0.0, d_o = (okd && io) ? __ldg(la + 2 * nx + xo) : 0.0;
+        const double ue = (ym && ie) ? __ldg(vm + xe) : 0.0, uo = (ym && io) ? __ldg(vm + xo) : 0.0;
+        const double we = (yp && ie) ? __ldg(vm + 2 * nx + xe) : 0.0, wo = (yp && io) ? __ldg(vm + 2 * nx + xo) : 0.0;
+        int e = max(max(max(fx_exp(ae), fx_exp(ao)), max(fx_exp(be), fx_exp(bo))), max(fx_exp(de), fx_exp(d_o)));
+        e = max(max(e, max(max(fx_exp(ue), fx_exp(uo)), max(fx_exp(we), fx_exp(wo)))), Ec[c]);
+        bad |= e > kFxMaxE;
+        const int ds = e - Ec[c];
+        const long long te = (fx_of(ae, e) + fx_of(be, e)) + fx_of(de, e);
+        const long long to = (fx_of(ao, e) + fx_of(bo, e)) + fx_of(d_o, e);
+        ce[c] = (shr_fx(tpe[c], ds) + te) + (fx_of(ue, e) + fx_of(we, e));  // off-line column sums at x
+        co[c] = (shr_fx(tpo[c], ds) + to) + (fx_of(uo, e) + fx_of(wo, e));
+        nte[c] = te;
+        nto[c] = to;
+        En[c] = e;
+      }
+      if (__any_sync(kFull, bad)) {  // huge or non-finite values: FP64 from this plane on
         fixed = false;
         break;
       }
-      long long ce[NC], co[NC], sh[NC];
-      const unsigned ds = (unsigned)(E - Ep);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const long long pe = ds < 64 ? tpe[c] >> ds : (tpe[c] < 0 ? -1LL : 0LL);  // earlier plane sums to the new scale
-        const long long po = ds < 64 ? tpo[c] >> ds : (tpo[c] < 0 ? -1LL : 0LL);
-        const long long te = (fx_of(ae[c], E) + fx_of(be[c], E)) + fx_of(de[c], E);
-        const long long to = (fx_of(ao[c], E) + fx_of(bo[c], E)) + fx_of(d_o[c], E);
-        ce[c] = (pe + te) + (fx_of(ue[c], E) + fx_of(we[c], E));  // off-line column sums at x
-        co[c] = (po + to) + (fx_of(uo[c], E) + fx_of(wo[c], E));
-        tpe[c] = te;
-        tpo[c] = to;
+        tpe[c] = nte[c];
+        tpo[c] = nto[c];
+        Ec[c] = En[c];
       }
-      Ep = E;
       double PE[NC], PO[NC];
-      prev_of_i<NC>(co, sh, lane);
+      {
+        long long sh[NC];
+        int Es[NC];
+        prev_of_i<NC>(co, sh, lane);  // column x-1 of an even x
+        prev_of_int<NC>(En, Es, lane);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) PE[c] = fx_to_double((sh[c] + ce[c]) + co[c], E);
-      next_of_i<NC>(ce, sh, lane);
+        for (int c = 0; c < NC; ++c) {
+          const int E3 = max(Es[c], En[c]);
+          PE[c] = fx_to_double((shr_fx(sh[c], E3 - Es[c]) + shr_fx(ce[c], E3 - En[c])) + shr_fx(co[c], E3 - En[c]), E3);
+        }
+        next_of_i<NC>(ce, sh, lane);  // column x+1 of an odd x
+        next_of_int<NC>(En, Es, lane);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) PO[c] = fx_to_double((ce[c] + co[c]) + sh[c], E);
+        for (int c = 0; c < NC; ++c) {
+          const int E3 = max(Es[c], En[c]);
+          PO[c] = fx_to_double((shr_fx(ce[c], E3 - En[c]) + shr_fx(co[c], E3 - En[c])) + shr_fx(sh[c], E3 - Es[c]), E3);
+        }
+      }
       pair_update<NC>(g, ii, zz, y, lane, pa, steps, own_valid, PE, PO, rg, zg, invd, tabc, rc, kap);
     }
-  } else {
-    tsum2<double, NC, false>(zg, nx, ny, nz, y, 2 * m0 + pz - 1, lane, tdpe, tdpo, vmask);
   }
   // FP64 sums for the remaining planes (rare: huge or non-finite values)
-  for (; m < m1; ++m) {
-    const int zz = 2 * m + pz;
-    double tne[NC], tno[NC], PE[NC], PO[NC], ce[NC], co[NC], sh[NC];
-    tsum2<double, NC, false>(zg, nx, ny, nz, y, zz + 1, lane, tne, tno, vmask);
-    const double *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
-    const double *lp = lm + 2 * nx;
+  if (m < m1) {
+    double tdpe[NC], tdpo[NC];
+    tsum2<double, NC, false>(zg, nx, ny, nz, y, 2 * m + pz - 1, lane, tdpe, tdpo, vmask);
+    for (; m < m1; ++m) {
+      const int zz = 2 * m + pz;
+      double tne[NC], tno[NC], PE[NC], PO[NC], ce[NC], co[NC], sh[NC];
+      tsum2<double, NC, false>(zg, nx, ny, nz, y, zz + 1, lane, tne, tno, vmask);
+      const double *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
+      const double *lp = lm + 2 * nx;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int xe = 2 * (lane + 32 * c), xo = xe + 1;
-      double ve = 0.0, vo = 0.0;
-      if (xe < nx) ve = (ym ? __ldg(lm + xe) : 0.0) + (yp ? __ldg(lp + xe) : 0.0);
-      if (xo < nx) vo = (ym ? __ldg(lm + xo) : 0.0) + (yp ? __ldg(lp + xo) : 0.0);
-      ce[c] = (tdpe[c] + tne[c]) + ve;
-      co[c] = (tdpo[c] + tno[c]) + vo;
-    }
-    prev_of<double, NC>(co, sh, lane);
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+        double ve = 0.0, vo = 0.0;
+        if (xe < nx) ve = (ym ? __ldg(lm + xe) : 0.0) + (yp ? __ldg(lp + xe) : 0.0);
+        if (xo < nx) vo = (ym ? __ldg(lm + xo) : 0.0) + (yp ? __ldg(lp + xo) : 0.0);
+        ce[c] = (tdpe[c] + tne[c]) + ve;
+        co[c] = (tdpo[c] + tno[c]) + vo;
+      }
+      prev_of<double, NC>(co, sh, lane);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) PE[c] = (sh[c] + ce[c]) + co[c];
-    next_of<double, NC>(ce, sh, lane);
+      for (int c = 0; c < NC; ++c) PE[c] = (sh[c] + ce[c]) + co[c];
+      next_of<double, NC>(ce, sh, lane);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) PO[c] = (ce[c] + co[c]) + sh[c];
-    pair_update<NC>(g, ii, zz, y, lane, pa, steps, own_valid, PE, PO, rg, zg, invd, tabc, rc, kap);
+      for (int c = 0; c < NC; ++c) PO[c] = (ce[c] + co[c]) + sh[c];
+      pair_update<NC>(g, ii, zz, y, lane, pa, steps, own_valid, PE, PO, rg, zg, invd, tabc, rc, kap);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      tdpe[c] = tne[c];
-      tdpo[c] = tno[c];
+      for (int c = 0; c < NC; ++c) {
+        tdpe[c] = tne[c];
+        tdpo[c] = tno[c];
+      }
     }
   }
 }
