@@ -265,7 +265,7 @@ def run_gpu(args):
 
     dev = torch.device("cuda", local)
     n = NX * NY * NZ
-    prob = HpcgProblem(NX, NY, NZ, levels=LEVELS, device=dev)
+    prob = HpcgProblem(NX, NY, NZ, levels=LEVELS, precision=args.precision, device=dev)
     if args.shapes:
         prob.set_launch_shapes(json.loads(args.shapes))
     b = prob.get_rhs()
@@ -402,7 +402,8 @@ def run_gpu(args):
                      "x": xs}
     # the same FP64 solve in other configurations of the library
     variants = {}
-    for name, kw in [("persistent_coarse_kernel", {"persistent": True}), ("plain_fp64_sums", {"fixed_point": False})]:
+    for name, kw in [("persistent_coarse_kernel", {"persistent": True}), ("plain_fp64_sums", {"fixed_point": False}),
+                     ("no_programmatic_dependent_launch", {"pdl": False})]:
         p_v = HpcgProblem(NX, NY, NZ, levels=LEVELS, device=dev, **kw)
         xv = torch.zeros(n, dtype=torch.float64, device=dev)
         p_v.pcg_solve(b, max_iters=ITERS, tol=0.0, out=xv)
@@ -498,6 +499,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=192, help="cubic grid edge (profiling runs; default 192)")
     ap.add_argument("--skip-forms", action="store_true", help="skip the batched and differentiable form timings")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="preconditioner precision of the timed solve (profiling runs; the bench line is FP64)")
     ap.add_argument("--shapes", default=None,
                     help="JSON list of per-level launch shapes [[row lines, row planes, line lines, line planes], ...] "
                          "to use instead of autotuning (repeatable profiling runs)")

@@ -72,6 +72,8 @@ typedef struct {
                        64-bit fixed point on the integer pipe (at least as accurate as FP64
                        summation; FP64 is used for steps with huge or non-finite values);
                        0: plain FP64 sums */
+  int pdl;          /* 1 (default): kernels are launched with programmatic dependent launch, so
+                       a kernel is scheduled while its predecessor finishes; 0: plain launches */
   int persistent;   /* 1: the smallest levels of the V-cycle run in one persistent cooperative
                        kernel (hpcg_persistent_levels); 0 (default): one launch per step, which
                        measured faster on one 192^3 grid (graph launches beat grid barriers) */

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <utility>
 #include <mutex>
 #include <vector>
 
@@ -18,6 +19,27 @@
 #include "hpcg_fixed.cuh"
 
 using namespace hpcg;
+
+// Kernel launch with programmatic dependent launch allowed: the kernel may be
+// scheduled while its predecessor in the stream still runs; every kernel of
+// this library starts with griddepcontrol.wait (pdl_enter), so it reads its
+// inputs only after the predecessor has finished.
+static thread_local bool t_pdl = true;  // set per call from the handle's option
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = t_pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // error plumbing (declared in hpcg_ctx.h)
@@ -260,6 +282,7 @@ static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s);
 static int build_tail_plans(hpcg_ctx *h);
 
 int ensure_ready(hpcg_ctx *h, cudaStream_t s) {
+  t_pdl = h->opt.pdl != 0;
   if (!h->ready) {
     char *p = nullptr;
     cudaError_t e = cudaMalloc(&p, h->need);
@@ -301,10 +324,10 @@ static int set_kappa_impl(hpcg_ctx *h, const double *kappa, cudaStream_t s) {
     if (l > 0) {
       const Inst &f = h->lv[l - 1].inst[0];
       const Inst &c = L.inst[0];
-      k_inject_kappa<<<grid_for(c.n), 256, 0, s>>>(f.nx, f.ny, c.nx, c.ny, c.nz, h->lv[l - 1].kap, L.kap);
+      launch_k(k_inject_kappa, grid_for(c.n), 256, 0, s, f.nx, f.ny, c.nx, c.ny, c.nz, h->lv[l - 1].kap, L.kap);
       CKL("k_inject_kappa");
     }
-    k_kappa_derived<<<grid_for(L.n), 256, 0, s>>>(L.n, L.kap, L.invd, L.kap32, L.invd32);
+    launch_k(k_kappa_derived, grid_for(L.n), 256, 0, s, L.n, L.kap, L.invd, L.kap32, L.invd32);
     CKL("k_kappa_derived");
   }
   h->has_kappa = true;
@@ -456,7 +479,7 @@ const float *invd_of<float>(const LevelData &L, bool has) { return has ? L.invd3
 template <typename T>
 static int enqueue_zero(hpcg_ctx *h, int l, T *v, cudaStream_t s, const CgState *st) {
   const LevelData &L = h->lv[l];
-  k_zero_inst<T><<<L.tab.nblk_red, kRedThreads, 0, s>>>(L.tab.inst, h->count, v, st);
+  launch_k(k_zero_inst<T>, L.tab.nblk_red, kRedThreads, 0, s, L.tab.inst, h->count, v, st);
   CKL("k_zero_inst");
   return HPCG_OK;
 }
@@ -467,12 +490,12 @@ static void launch_gs_lines(const LevelData &L, int count, int py, int pz, int p
   const dim3 grid(L.tab.nblk_line), block(32, L.tab.line_lpc);
   if constexpr (sizeof(T) == 8) {
     if (fixed && NCH <= 6) {  // longer lines would spill registers: plain FP64 sums
-      k_gs_lines_fx<NCH><<<grid, block, 0, s>>>(L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa, steps, vmask, r, z, invd,
+      launch_k(k_gs_lines_fx<NCH>, grid, block, 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa, steps, vmask, r, z, invd,
                                                 st, tabc, rc, kap);
       return;
     }
   }
-  k_gs_lines<T, NCH><<<grid, block, 0, s>>>(L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa, steps, vmask, r, z, invd, st,
+  launch_k(k_gs_lines<T, NCH>, grid, block, 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa, steps, vmask, r, z, invd, st,
                                             tabc, rc, kap);
 }
 
@@ -499,7 +522,7 @@ static int enqueue_line_steps(hpcg_ctx *h, int l, int py, int pz, int pa, int st
       if (rc || vmask != 0xF) return HPCG_ERR_UNSUPPORTED;
       for (int k = 0; k < steps; ++k) {
         const int px = (k & 1) ? 1 - pa : pa;
-        k_gs_color<T><<<L.tab.nblk_half, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, px, py, pz, r, z, invd, st);
+        launch_k(k_gs_color<T>, L.tab.nblk_half, dim3(kTileX, kTileY), 0, s, L.tab.inst, h->count, px, py, pz, r, z, invd, st);
         CKL("k_gs_color");
       }
       return HPCG_OK;
@@ -556,12 +579,12 @@ static void launch_spmv_lines(hpcg_ctx *h, const LevelData &L, const T *x, const
   const dim3 blk(32, L.tab.row_lpc);
   if constexpr (sizeof(T) == 8 && N <= 8) {
     if (h->opt.fixed_point) {
-      k_spmv_lines_fx<N, Mode><<<L.tab.nblk_row, blk, 0, s>>>(L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, partials,
+      launch_k(k_spmv_lines_fx<N, Mode>, L.tab.nblk_row, blk, 0, s, L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, partials,
                                                               st);
       return;
     }
   }
-  k_spmv_lines<T, N, Mode><<<L.tab.nblk_row, blk, 0, s>>>(L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, partials, st);
+  launch_k(k_spmv_lines<T, N, Mode>, L.tab.nblk_row, blk, 0, s, L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, partials, st);
 }
 
 template <typename T, int Mode>
@@ -577,7 +600,7 @@ static int enqueue_spmv(hpcg_ctx *h, int l, const T *x, const T *b, T *y, const 
     HPCG_SP_CASE(7) HPCG_SP_CASE(8) HPCG_SP_CASE(10) HPCG_SP_CASE(12) HPCG_SP_CASE(16)
 #undef HPCG_SP_CASE
     default:  // lines longer than the register window: one thread per row (partials per 32x8 tile)
-      k_spmv<T, Mode><<<L.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L.tab.inst, h->count, x, b, y, kap, partials, st);
+      launch_k(k_spmv<T, Mode>, L.tab.nblk_full, dim3(kTileX, kTileY), 0, s, L.tab.inst, h->count, x, b, y, kap, partials, st);
       break;
   }
   CKL("k_spmv_lines");
@@ -587,7 +610,7 @@ static int enqueue_spmv(hpcg_ctx *h, int l, const T *x, const T *b, T *y, const 
 template <typename T>
 static int enqueue_restrict(hpcg_ctx *h, int l, const T *r, const T *z, T *rc, cudaStream_t s, const CgState *st) {
   const LevelData &F = h->lv[l], &C = h->lv[l + 1];
-  k_restrict_residual<T><<<C.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(F.tab.inst, C.tab.inst, h->count, r, z, rc,
+  launch_k(k_restrict_residual<T>, C.tab.nblk_full, dim3(kTileX, kTileY), 0, s, F.tab.inst, C.tab.inst, h->count, r, z, rc,
                                                                           kap_of<T>(F, h->has_kappa), st);
   CKL("k_restrict_residual");
   return HPCG_OK;
@@ -596,7 +619,7 @@ static int enqueue_restrict(hpcg_ctx *h, int l, const T *r, const T *z, T *rc, c
 template <typename T>
 static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s, const CgState *st) {
   const LevelData &F = h->lv[l], &C = h->lv[l + 1];
-  k_prolong_add<T><<<C.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(F.tab.inst, C.tab.inst, h->count, zc, z, st);
+  launch_k(k_prolong_add<T>, C.tab.nblk_full, dim3(kTileX, kTileY), 0, s, F.tab.inst, C.tab.inst, h->count, zc, z, st);
   CKL("k_prolong_add");
   return HPCG_OK;
 }
@@ -637,19 +660,22 @@ static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_
   return HPCG_OK;
 }
 
-// z = M r on level-0 FP64 vectors, in the handle's precision.
-static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st) {
+// z = M r on level-0 FP64 vectors, in the handle's precision.  r32_current:
+// the FP32 copy of r (level-0 r32) is already up to date (the CG update wrote it).
+static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st, bool r32_current = false) {
   if (h->opt.precision == HPCG_MIXED) {
     const LevelData &L0 = h->lv[0];
-    k_convert<double, float><<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, r, L0.r32, st);
-    CKL("k_convert");
+    if (!r32_current) {
+      launch_k(k_convert<double, float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, r, L0.r32, st);
+      CKL("k_convert");
+    }
     float *rl[kMaxLevels], *zl[kMaxLevels];
     for (int l = 0; l < h->levels; ++l) {
       rl[l] = h->lv[l].r32;
       zl[l] = h->lv[l].z32;
     }
     TRY(enqueue_vcycle_t<float>(h, rl, zl, s, st));
-    k_convert<float, double><<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, L0.z32, z, st);
+    launch_k(k_convert<float, double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, L0.z32, z, st);
     CKL("k_convert");
     return HPCG_OK;
   }
@@ -681,10 +707,15 @@ static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_ite
   const LevelData &L0 = h->lv[0];
   // r = b - A x
   TRY((enqueue_spmv<double, 1>(h, 0, x, b, h->cg_r, h->has_kappa ? L0.kap : nullptr, nullptr, nullptr, s)));
-  k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_r, h->part, h->st);
+  launch_k(k_dot_partial, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, h->cg_r, h->part, h->st);
   CKL("k_dot_partial");
-  k_finalize<FIN_NORM0><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  launch_k(k_finalize<FIN_NORM0>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<NORM0>");
+  if (h->opt.precision == HPCG_MIXED) {  // FP32 copy of the initial residual for the preconditioner
+    launch_k(k_convert<double, float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_r, L0.r32,
+             (const CgState *)nullptr);
+    CKL("k_convert");
+  }
   if (max_iters <= 0) {
     // nothing to iterate: mark every instance done
   }
@@ -694,23 +725,25 @@ static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_ite
 static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_t s) {
   const LevelData &L0 = h->lv[0];
   const double *kap = h->has_kappa ? L0.kap : nullptr;
-  if (h->opt.precision == HPCG_MIXED) {
-    k_restart_residual<<<L0.tab.nblk_full, dim3(kTileX, kTileY), 0, s>>>(L0.tab.inst, h->count, x, b, h->cg_r, kap, h->st);
+  const bool mixed = h->opt.precision == HPCG_MIXED;
+  if (mixed) {
+    launch_k(k_restart_residual, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, x, b, h->cg_r, L0.r32, kap, h->st);
     CKL("k_restart_residual");
   }
-  TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st));  // z = M r
-  k_dot_partial<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_r, h->cg_z, h->part, h->st);
+  TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st, mixed));  // z = M r (r32 kept current by the CG updates)
+  launch_k(k_dot_partial, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, h->cg_z, h->part, h->st);
   CKL("k_dot_partial");
-  k_finalize<FIN_RTZ><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  launch_k(k_finalize<FIN_RTZ>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<RTZ>");
-  k_update_p<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_z, h->cg_p, h->st);  // p = z + beta p
+  launch_k(k_update_p, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_z, h->cg_p, h->st);  // p = z + beta p
   CKL("k_update_p");
   TRY((enqueue_spmv<double, 0>(h, 0, h->cg_p, nullptr, h->cg_ap, kap, h->part, h->st, s)));  // Ap, p.Ap partials
-  k_finalize<FIN_PAP><<<h->count, kFinThreads, 0, s>>>(L0.tab.inst, h->count, h->part, L0.tab.nch ? 2 : 1, h->st, h->hist, nullptr);
+  launch_k(k_finalize<FIN_PAP>, h->count, kFinThreads, 0, s, L0.tab.inst, h->count, h->part, L0.tab.nch ? 2 : 1, h->st, h->hist, nullptr);
   CKL("k_finalize<PAP>");
-  k_update_xr<<<L0.tab.nblk_red, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r, h->part, h->st);
+  launch_k(k_update_xr, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r,
+           mixed ? L0.r32 : nullptr, h->part, h->st);
   CKL("k_update_xr");
-  k_finalize<FIN_NORM><<<h->count, kRedThreads, 0, s>>>(L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+  launch_k(k_finalize<FIN_NORM>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<NORM>");
   return HPCG_OK;
 }
@@ -866,11 +899,13 @@ static int time_shape(hpcg_ctx *h, int l, bool rows, int lpc, int zc, cudaStream
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   int rc = HPCG_OK;
-  const int reps = 3;
+  const int reps = 6;
   for (int it = 0; it <= reps && rc == HPCG_OK; ++it) {
     if (it == 1) cudaEventRecord(e0, s);
     if (rows)
       rc = enqueue_spmv<double, 0>(h, l, a, nullptr, b, nullptr, nullptr, nullptr, s);
+    else if (h->opt.precision == HPCG_MIXED)  // the V-cycle runs the FP32 kernel
+      rc = enqueue_line_steps<float>(h, l, 0, 0, 0, 2, L.r32, L.z32, s, nullptr);
     else
       rc = enqueue_line_steps<double>(h, l, 0, 0, 0, 2, a, b, s, nullptr);
   }
@@ -896,6 +931,10 @@ static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s) {
     double *b = l == 0 ? h->cg_z : L.z;
     CK(cudaMemsetAsync(a, 0, sizeof(double) * L.n, s));
     CK(cudaMemsetAsync(b, 0, sizeof(double) * L.n, s));
+    if (h->opt.precision == HPCG_MIXED) {
+      CK(cudaMemsetAsync(L.r32, 0, sizeof(float) * L.n, s));
+      CK(cudaMemsetAsync(L.z32, 0, sizeof(float) * L.n, s));
+    }
     for (int pass = 0; pass < 2; ++pass) {
       const bool rows = pass == 0;
       float best = 1e30f;
@@ -1025,6 +1064,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->max_rhs = 0;
   opt->autotune = 1;
   opt->fixed_point = 1;
+  opt->pdl = 1;
   opt->persistent = 0;
   return HPCG_OK;
 }
@@ -1126,7 +1166,7 @@ int hpcg_level_dims(hpcg_handle h, int level, int *dims_host) {
 int hpcg_get_colors(hpcg_handle h, int level, int *colors_dev, void *stream) {
   if (!h || !colors_dev || level < 0 || level >= h->levels) return HPCG_ERR_INVALID_ARG;
   const Inst &g = h->lv[level].inst[0];
-  k_colors<<<grid_for(g.n), 256, 0, (cudaStream_t)stream>>>(g.nx, g.ny, g.nz, colors_dev);
+  launch_k(k_colors, grid_for(g.n), 256, 0, (cudaStream_t)stream, g.nx, g.ny, g.nz, colors_dev);
   CKL("k_colors");
   return HPCG_OK;
 }
@@ -1134,7 +1174,7 @@ int hpcg_get_colors(hpcg_handle h, int level, int *colors_dev, void *stream) {
 int hpcg_get_f2c(hpcg_handle h, int level, int *f2c_dev, void *stream) {
   if (!h || !f2c_dev || level < 0 || level >= h->levels - 1) return HPCG_ERR_INVALID_ARG;
   const Inst &f = h->lv[level].inst[0], &c = h->lv[level + 1].inst[0];
-  k_f2c<<<grid_for(c.n), 256, 0, (cudaStream_t)stream>>>(f.nx, f.ny, c.nx, c.ny, c.nz, f2c_dev);
+  launch_k(k_f2c, grid_for(c.n), 256, 0, (cudaStream_t)stream, f.nx, f.ny, c.nx, c.ny, c.nz, f2c_dev);
   CKL("k_f2c");
   return HPCG_OK;
 }
@@ -1142,7 +1182,7 @@ int hpcg_get_f2c(hpcg_handle h, int level, int *f2c_dev, void *stream) {
 int hpcg_get_row_nnz(hpcg_handle h, int level, int *nnz_dev, void *stream) {
   if (!h || !nnz_dev || level < 0 || level >= h->levels) return HPCG_ERR_INVALID_ARG;
   const Inst &g = h->lv[level].inst[0];
-  k_row_nnz<<<grid_for(g.n), 256, 0, (cudaStream_t)stream>>>(g.nx, g.ny, g.nz, nnz_dev);
+  launch_k(k_row_nnz, grid_for(g.n), 256, 0, (cudaStream_t)stream, g.nx, g.ny, g.nz, nnz_dev);
   CKL("k_row_nnz");
   return HPCG_OK;
 }
@@ -1154,7 +1194,7 @@ int hpcg_get_rhs(hpcg_handle h, double *b_dev, void *stream) {
   TRY(ensure_ready(h, s));
   for (int i = 0; i < h->count; ++i) {
     const Inst &g = h->lv[0].inst[i];
-    k_rhs_ones<<<grid_for(g.n), 256, 0, s>>>(g.nx, g.ny, g.nz, h->has_kappa ? h->lv[0].kap : nullptr, b_dev + g.off);
+    launch_k(k_rhs_ones, grid_for(g.n), 256, 0, s, g.nx, g.ny, g.nz, h->has_kappa ? h->lv[0].kap : nullptr, b_dev + g.off);
     CKL("k_rhs_ones");
   }
   return HPCG_OK;
@@ -1216,9 +1256,9 @@ int hpcg_dot(hpcg_handle h, long n, const double *a_dev, const double *b_dev, do
   std::lock_guard<std::mutex> lk(h->mu);
   cudaStream_t s = (cudaStream_t)stream;
   TRY(ensure_ready(h, s));
-  k_dot_raw<<<kRawDotBlocks, kRedThreads, 0, s>>>(n, a_dev, b_dev, h->part);
+  launch_k(k_dot_raw, kRawDotBlocks, kRedThreads, 0, s, n, a_dev, b_dev, h->part);
   CKL("k_dot_raw");
-  k_sum_raw<<<1, kRedThreads, 0, s>>>(kRawDotBlocks, h->part, out_dev);
+  launch_k(k_sum_raw, 1, kRedThreads, 0, s, kRawDotBlocks, h->part, out_dev);
   CKL("k_sum_raw");
   return HPCG_OK;
 }
@@ -1228,7 +1268,7 @@ int hpcg_waxpby(hpcg_handle h, long n, double alpha, const double *x_dev, double
   if (!h || n < 0) return HPCG_ERR_INVALID_ARG;
   if (n == 0) return HPCG_OK;
   if (!x_dev || !y_dev || !w_dev) return HPCG_ERR_INVALID_ARG;
-  k_waxpby<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, alpha, x_dev, beta, y_dev, w_dev);
+  launch_k(k_waxpby, grid_for(n), 256, 0, (cudaStream_t)stream, n, alpha, x_dev, beta, y_dev, w_dev);
   CKL("k_waxpby");
   return HPCG_OK;
 }
@@ -1298,7 +1338,7 @@ int hpcg_pcg_backward(hpcg_handle h, const double *x_dev, const double *grad_x_d
   int rc = run_pcg(h, grad_x_dev, grad_b_dev, max_iters, rel_tol, stats, s);  // A lambda = grad_x
   if (rc != HPCG_OK && rc != HPCG_ERR_NOT_CONVERGED) return rc;
   if (grad_kappa_dev) {
-    k_grad_kappa<<<grid_for(n), 256, 0, s>>>(n, grad_b_dev, x_dev, grad_kappa_dev);
+    launch_k(k_grad_kappa, grid_for(n), 256, 0, s, n, grad_b_dev, x_dev, grad_kappa_dev);
     CKL("k_grad_kappa");
   }
   return rc;

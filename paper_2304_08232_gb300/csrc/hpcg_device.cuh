@@ -6,6 +6,14 @@
 
 namespace hpcg {
 
+// Programmatic dependent launch: wait until the preceding kernel has finished
+// and its writes are visible.  Blocks signal their dependents implicitly when
+// they exit, so the next kernel is launched as this one drains instead of
+// after its completion is processed (an explicit early signal measured slower:
+// it places the next grid's first wave while this one still runs).  Without
+// the launch attribute: a no-op.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Sum of the 26 neighbours of (x,y,z) that lie inside the grid, in ascending
 // column order.  v points at the grid's first row.
 template <typename T>

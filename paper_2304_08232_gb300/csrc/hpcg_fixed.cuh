@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ ta
                                                      const double *__restrict__ invd, const CgState *__restrict__ st,
                                                      const Inst *__restrict__ tabc, double *__restrict__ rc,
                                                      const double *__restrict__ kap) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<4>(tab, count, blk);
   const Inst g = tab[ii];
@@ -403,6 +404,7 @@ template <int NC, int Mode>
 __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ tab, int count, int lpc, int zc, const double *__restrict__ x,
                                                        const double *__restrict__ b, double *__restrict__ y, const double *__restrict__ kap,
                                                        double *__restrict__ partials, const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<3>(tab, count, blk);
   const Inst g = tab[ii];

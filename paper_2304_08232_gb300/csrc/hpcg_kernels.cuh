@@ -20,6 +20,7 @@ template <typename T, int Mode>
 __global__ void __launch_bounds__(kBlock) k_spmv(const Inst *__restrict__ tab, int count, const T *__restrict__ x,
                                                  const T *__restrict__ b, T *__restrict__ y, const T *__restrict__ kap,
                                                  double *__restrict__ partials, const CgState *__restrict__ st) {
+  pdl_enter();
   __shared__ double sh[kBlock / 32];
   const int blk = blockIdx.x;
   const int ii = find_inst<0>(tab, count, blk);
@@ -52,27 +53,27 @@ __global__ void __launch_bounds__(kBlock) k_spmv(const Inst *__restrict__ tab, i
   }
 }
 
-// Restart of the mixed-precision outer loop: r = b - A x for instances whose
-// stall flag is set (FP64).
-__global__ void __launch_bounds__(kBlock) k_restart_residual(const Inst *__restrict__ tab, int count, const double *__restrict__ x,
-                                                             const double *__restrict__ b, double *__restrict__ r,
-                                                             const double *__restrict__ kap, const CgState *__restrict__ st) {
+// Restart of the mixed-precision outer loop: r = b - A x (FP64) for instances
+// whose stall flag is set, and the FP32 copy of r the preconditioner reads.
+// A small grid-stride launch: it costs little in the (usual) iterations that
+// do not restart.
+__global__ void __launch_bounds__(kRedThreads) k_restart_residual(const Inst *__restrict__ tab, int count, const double *__restrict__ x,
+                                                                  const double *__restrict__ b, double *__restrict__ r,
+                                                                  float *__restrict__ r32, const double *__restrict__ kap,
+                                                                  const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
-  const int ii = find_inst<0>(tab, count, blk);
+  const int ii = find_inst<2>(tab, count, blk);
   const Inst g = tab[ii];
   if (st[ii].done || !st[ii].restart) return;
-  int lb = blk - g.blk_full;
-  const int tx = (g.nx + kTileX - 1) / kTileX, ty = (g.ny + kTileY - 1) / kTileY;
-  const int bx = lb % tx;
-  lb /= tx;
-  const int by = lb % ty;
-  const int z = lb / ty;
-  const int xx = bx * kTileX + threadIdx.x, yy = by * kTileY + threadIdx.y;
-  if (xx < g.nx && yy < g.ny && z < g.nz) {
-    const double *xg = x + g.off;
-    const long li = xx + (long)g.nx * (yy + (long)g.ny * z);
+  const double *xg = x + g.off;
+  const long stride = (long)g.nred * kRedThreads;
+  for (long li = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; li < g.n; li += stride) {
+    const int xx = (int)(li % g.nx), yy = (int)((li / g.nx) % g.ny), zz = (int)(li / ((long)g.nx * g.ny));
     const long gi = g.off + li;
-    r[gi] = b[gi] - (diag_of(kap, gi) * xg[li] - nbr_sum26(xg, xx, yy, z, g.nx, g.ny, g.nz));
+    const double rn = b[gi] - (diag_of(kap, gi) * xg[li] - nbr_sum26(xg, xx, yy, zz, g.nx, g.ny, g.nz));
+    r[gi] = rn;
+    if (r32) r32[gi] = (float)rn;
   }
 }
 
@@ -83,6 +84,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_gs_color(const Inst *__restrict__ tab, int count, int px, int py, int pz,
                                                      const T *__restrict__ r, T *__restrict__ z, const T *__restrict__ invd,
                                                      const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<1>(tab, count, blk);
   const Inst g = tab[ii];
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_restrict_residual(const Inst *__rest
                                                               const T *__restrict__ r, const T *__restrict__ z,
                                                               T *__restrict__ rc, const T *__restrict__ kapf,
                                                               const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<0>(tabc, count, blk);
   const Inst c = tabc[ii];
@@ -140,6 +143,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong_add(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count,
                                                         const T *__restrict__ zc, T *__restrict__ z,
                                                         const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<0>(tabc, count, blk);
   const Inst c = tabc[ii];
@@ -161,6 +165,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(const Inst *__restrict__
 // Zero the vectors of every instance not yet converged (level vector z before smoothing).
 template <typename T>
 __global__ void k_zero_inst(const Inst *__restrict__ tab, int count, T *__restrict__ v, const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<2>(tab, count, blk);
   const Inst g = tab[ii];
@@ -173,6 +178,7 @@ __global__ void k_zero_inst(const Inst *__restrict__ tab, int count, T *__restri
 template <typename Tin, typename Tout>
 __global__ void k_convert(const Inst *__restrict__ tab, int count, const Tin *__restrict__ in, Tout *__restrict__ out,
                           const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<2>(tab, count, blk);
   const Inst g = tab[ii];
@@ -192,6 +198,7 @@ __global__ void k_convert(const Inst *__restrict__ tab, int count, const Tin *__
 __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const Inst *__restrict__ tab, int count, const double *__restrict__ a,
                                                              const double *__restrict__ bv, double *__restrict__ partials,
                                                              const CgState *__restrict__ st) {
+  pdl_enter();
   __shared__ double sh[kRedThreads / 32];
   const int blk = blockIdx.x;
   const int ii = find_inst<2>(tab, count, blk);
@@ -220,6 +227,7 @@ template <int Kind>
 __global__ void __launch_bounds__(kFinThreads) k_finalize(const Inst *__restrict__ tab, int count, const double *__restrict__ partials,
                                                           int stencil, CgState *__restrict__ st, double *__restrict__ hist,
                                                           double *__restrict__ out) {
+  pdl_enter();
   __shared__ double sh[kFinThreads / 32];
   const int ii = blockIdx.x;
   const Inst g = tab[ii];
@@ -247,6 +255,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const Inst *__restrict
 // p = z + beta p (p = z on the first iteration or after a restart)
 __global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict__ tab, int count, const double *__restrict__ zv,
                                                           double *__restrict__ p, const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<2>(tab, count, blk);
   const Inst g = tab[ii];
@@ -264,8 +273,9 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict
 // x += alpha p; r -= alpha Ap; partials of r.r
 __global__ void __launch_bounds__(kRedThreads) k_update_xr(const Inst *__restrict__ tab, int count, const double *__restrict__ p,
                                                            const double *__restrict__ ap, double *__restrict__ x,
-                                                           double *__restrict__ r, double *__restrict__ partials,
+                                                           double *__restrict__ r, float *__restrict__ r32, double *__restrict__ partials,
                                                            const CgState *__restrict__ st) {
+  pdl_enter();
   __shared__ double sh[kRedThreads / 32];
   const int blk = blockIdx.x;
   const int ii = find_inst<2>(tab, count, blk);
@@ -280,6 +290,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(const Inst *__restric
       x[gi] = x[gi] + alpha * p[gi];
       const double rn = r[gi] - alpha * ap[gi];
       r[gi] = rn;
+      if (r32) r32[gi] = (float)rn;  // the FP32 preconditioner's copy (mixed precision)
       s += rn * rn;
     }
   }
@@ -290,6 +301,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(const Inst *__restric
 // Plain dot product of two raw arrays with a fixed grid (deterministic).
 __global__ void __launch_bounds__(kRedThreads) k_dot_raw(long n, const double *__restrict__ a, const double *__restrict__ b,
                                                          double *__restrict__ partials) {
+  pdl_enter();
   __shared__ double sh[kRedThreads / 32];
   double s = 0.0;
   for (long i = blockIdx.x * (long)kRedThreads + threadIdx.x; i < n; i += (long)gridDim.x * kRedThreads) s += a[i] * b[i];
@@ -298,6 +310,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_raw(long n, const double *_
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_sum_raw(int cnt, const double *__restrict__ partials, double *__restrict__ out) {
+  pdl_enter();
   __shared__ double sh[kRedThreads / 32];
   const double s = sum_partials(partials, 0, cnt, sh);
   if (threadIdx.x == 0) out[0] = s;
@@ -306,12 +319,14 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_raw(int cnt, const double *
 // w = alpha x + beta y over n values (grid-stride)
 __global__ void k_waxpby(long n, double alpha, const double *__restrict__ x, double beta, const double *__restrict__ y,
                          double *__restrict__ w) {
+  pdl_enter();
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     w[i] = alpha * x[i] + beta * y[i];
 }
 
 // grad_kappa_i = -lambda_i x_i (diagonal of the outer product -lambda x^T)
 __global__ void k_grad_kappa(long n, const double *__restrict__ lam, const double *__restrict__ x, double *__restrict__ gk) {
+  pdl_enter();
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) gk[i] = -lam[i] * x[i];
 }
 
@@ -319,6 +334,7 @@ __global__ void k_grad_kappa(long n, const double *__restrict__ lam, const doubl
 // Setup kernels (Section II-B input generation, Section III-A colouring,
 // Section II-E injection), one thread per row.
 __global__ void k_colors(int nx, int ny, int nz, int *__restrict__ out) {
+  pdl_enter();
   const long n = (long)nx * ny * nz;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
@@ -327,6 +343,7 @@ __global__ void k_colors(int nx, int ny, int nz, int *__restrict__ out) {
 }
 
 __global__ void k_row_nnz(int nx, int ny, int nz, int *__restrict__ out) {
+  pdl_enter();
   const long n = (long)nx * ny * nz;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
@@ -337,6 +354,7 @@ __global__ void k_row_nnz(int nx, int ny, int nz, int *__restrict__ out) {
 
 // b = A * ones: b_i = 26 + kappa_i - (nnz_i - 1)
 __global__ void k_rhs_ones(int nx, int ny, int nz, const double *__restrict__ kap, double *__restrict__ b) {
+  pdl_enter();
   const long n = (long)nx * ny * nz;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
@@ -346,6 +364,7 @@ __global__ void k_rhs_ones(int nx, int ny, int nz, const double *__restrict__ ka
 }
 
 __global__ void k_f2c(int nxf, int nyf, int nxc, int nyc, int nzc, int *__restrict__ out) {
+  pdl_enter();
   const long n = (long)nxc * nyc * nzc;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const int xc = (int)(c % nxc), yc = (int)((c / nxc) % nyc), zc = (int)(c / ((long)nxc * nyc));
@@ -357,6 +376,7 @@ __global__ void k_f2c(int nxf, int nyf, int nxc, int nyc, int nzc, int *__restri
 // inverse diagonal 1/(26 + kappa) of level l+1 in both precisions.
 __global__ void k_inject_kappa(int nxf, int nyf, int nxc, int nyc, int nzc, const double *__restrict__ kf,
                                double *__restrict__ kc) {
+  pdl_enter();
   const long n = (long)nxc * nyc * nzc;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const int xc = (int)(c % nxc), yc = (int)((c / nxc) % nyc), zc = (int)(c / ((long)nxc * nyc));
@@ -366,6 +386,7 @@ __global__ void k_inject_kappa(int nxf, int nyf, int nxc, int nyc, int nzc, cons
 
 __global__ void k_kappa_derived(long n, const double *__restrict__ k, double *__restrict__ invd, float *__restrict__ k32,
                                 float *__restrict__ invd32) {
+  pdl_enter();
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const double d = 26.0 + k[i];
     invd[i] = 1.0 / d;

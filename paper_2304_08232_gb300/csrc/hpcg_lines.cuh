@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, 
                                                   int steps, int vmask, const T *__restrict__ r, T *__restrict__ z,
                                                   const T *__restrict__ invd, const CgState *__restrict__ st, const Inst *__restrict__ tabc,
                                                   T *__restrict__ rc, const T *__restrict__ kap) {
+  pdl_enter();
   gs_lines_vblock<T, NC>(blockIdx.x, threadIdx.y, tab, count, lpc, zc, py, pz, pa, steps, vmask, r, z, invd, st, tabc, rc, kap);
 }
 
@@ -269,6 +270,7 @@ template <typename T, int NCH, int Mode>
 __global__ void __launch_bounds__(256) k_spmv_lines(const Inst *__restrict__ tab, int count, int lpc, int zc, const T *__restrict__ x,
                                                     const T *__restrict__ b, T *__restrict__ y, const T *__restrict__ kap,
                                                     double *__restrict__ partials, const CgState *__restrict__ st) {
+  pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<3>(tab, count, blk);
   const Inst g = tab[ii];
