@@ -498,6 +498,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=192, help="cubic grid edge (profiling runs; default 192)")
+    ap.add_argument("--dims", default=None, help="nx,ny,nz of a non-cubic grid (profiling runs; overrides --grid)")
     ap.add_argument("--skip-forms", action="store_true", help="skip the batched and differentiable form timings")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="preconditioner precision of the timed solve (profiling runs; the bench line is FP64)")
@@ -509,6 +510,8 @@ def main():
     args = ap.parse_args()
     global NX, NY, NZ
     NX = NY = NZ = args.grid
+    if args.dims:
+        NX, NY, NZ = (int(v) for v in args.dims.split(","))
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -662,7 +662,8 @@ static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_
 
 // z = M r on level-0 FP64 vectors, in the handle's precision.  r32_current:
 // the FP32 copy of r (level-0 r32) is already up to date (the CG update wrote it).
-static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st, bool r32_current = false) {
+static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st, bool r32_current = false,
+                          bool keep_z32 = false) {
   if (h->opt.precision == HPCG_MIXED) {
     const LevelData &L0 = h->lv[0];
     if (!r32_current) {
@@ -675,8 +676,10 @@ static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t 
       zl[l] = h->lv[l].z32;
     }
     TRY(enqueue_vcycle_t<float>(h, rl, zl, s, st));
-    launch_k(k_convert<float, double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, L0.z32, z, st);
-    CKL("k_convert");
+    if (!keep_z32) {
+      launch_k(k_convert<float, double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, L0.z32, z, st);
+      CKL("k_convert");
+    }
     return HPCG_OK;
   }
   double *rl[kMaxLevels], *zl[kMaxLevels];
@@ -707,7 +710,7 @@ static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_ite
   const LevelData &L0 = h->lv[0];
   // r = b - A x
   TRY((enqueue_spmv<double, 1>(h, 0, x, b, h->cg_r, h->has_kappa ? L0.kap : nullptr, nullptr, nullptr, s)));
-  launch_k(k_dot_partial, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, h->cg_r, h->part, h->st);
+  launch_k(k_dot_partial<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, h->cg_r, h->part, h->st);
   CKL("k_dot_partial");
   launch_k(k_finalize<FIN_NORM0>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<NORM0>");
@@ -730,12 +733,22 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
     launch_k(k_restart_residual, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, x, b, h->cg_r, L0.r32, kap, h->st);
     CKL("k_restart_residual");
   }
-  TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st, mixed));  // z = M r (r32 kept current by the CG updates)
-  launch_k(k_dot_partial, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, h->cg_z, h->part, h->st);
+  // z = M r; mixed precision leaves z in FP32 (level-0 z32), which the dot and
+  // the p update read directly (r32 is kept current by the CG updates)
+  TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st, mixed, mixed));
+  if (mixed)
+    launch_k(k_dot_partial<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, (const float *)L0.z32, h->part,
+             h->st);
+  else
+    launch_k(k_dot_partial<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, (const double *)h->cg_z, h->part,
+             h->st);
   CKL("k_dot_partial");
   launch_k(k_finalize<FIN_RTZ>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<RTZ>");
-  launch_k(k_update_p, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_z, h->cg_p, h->st);  // p = z + beta p
+  if (mixed)
+    launch_k(k_update_p<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const float *)L0.z32, h->cg_p, h->st);
+  else
+    launch_k(k_update_p<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_z, h->cg_p, h->st);
   CKL("k_update_p");
   TRY((enqueue_spmv<double, 0>(h, 0, h->cg_p, nullptr, h->cg_ap, kap, h->part, h->st, s)));  // Ap, p.Ap partials
   launch_k(k_finalize<FIN_PAP>, h->count, kFinThreads, 0, s, L0.tab.inst, h->count, h->part, L0.tab.nch ? 2 : 1, h->st, h->hist, nullptr);

@@ -41,11 +41,23 @@ __device__ __forceinline__ long long fx_of(double v, int E) {
   return ((long long)q ^ s) - s;
 }
 
-// q 2^(E-1080) as FP64: one rounding (int64 -> double), then an exact scale.
+// q 2^(E-1080) as FP64, rounded to nearest (ties to even), built from the
+// bits of q on the integer pipe: an int64 -> double conversion instruction
+// occupies the FP64 pipe for several of its issue slots on this GPU.
+// E in [kFxMinE, kFxMaxE] keeps the result a normal number.
 __device__ __forceinline__ double fx_to_double(long long q, int E) {
-  const double d = (double)q;
-  const long long bits = __double_as_longlong(d) + ((long long)(E - 1080) << 52);
-  return q == 0 ? 0.0 : __longlong_as_double(bits);
+  const unsigned long long sign = (unsigned long long)q & 0x8000000000000000ULL;
+  const unsigned long long a = q < 0 ? 0ULL - (unsigned long long)q : (unsigned long long)q;  // |q| < 2^63
+  const int lz = __clzll(a);                                  // >= 1 for a != 0
+  const unsigned long long m = a << lz;                        // leading one at bit 63
+  const unsigned long long mant = m >> 11;                     // 53 significant bits
+  const unsigned long long rbit = (m >> 10) & 1ULL;            // first dropped bit
+  const unsigned long long sticky = (m & 0x3FFULL) != 0ULL;    // any further dropped bit
+  const unsigned long long up = rbit & (sticky | (mant & 1ULL));
+  // |value| = m 2^(E - 1080 - lz); biased exponent of the leading one: E + 6 - lz.
+  // A carry out of the mantissa rounding moves into the exponent field.
+  const unsigned long long bits = ((unsigned long long)(E + 6 - lz) << 52) + (mant - (1ULL << 52)) + up;
+  return a == 0ULL ? 0.0 : __longlong_as_double((long long)(bits | sign));
 }
 
 __device__ __forceinline__ int warp_max(int v) {
@@ -189,10 +201,13 @@ __device__ __forceinline__ void next_of_int(const int (&v)[NC], int (&out)[NC], 
 }
 
 // Colour-pair kernel (see k_gs_lines) with the off-line sums in fixed point.
-// Every lane scales each of its 32-wide chunks (the x pair 2k, 2k+1) by that
-// chunk's own exponent bound, so only one chunk's raw values are live at a
-// time; the x-window sum aligns the three columns it adds to their largest
-// bound.  Bounds only grow along z within a block's planes.
+// Every lane scales each of its 32-wide chunks (the x pair 2k, 2k+1) on its
+// own, so only one chunk's raw values are live at a time.  Each plane sum T
+// (over y-1..y+1) is kept at the scale of its own three lines; a step adds T
+// below, T above and the two lines beside at the largest scale of the four,
+// and the x-window sum aligns the three columns it adds to their largest
+// scale.  Every scale depends only on the values summed, never on how planes
+// are grouped into blocks, so results do not depend on the launch shape.
 template <int NC>
 __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
                                                      int steps, int vmask, const double *__restrict__ r, double *__restrict__ z,
@@ -256,7 +271,7 @@ __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ ta
       const double *vm = zg + (long)zz * sxy + (long)(y - 1) * nx;
       const bool oka = zin && y - 1 >= 0 && vyo, okb = zin && vy0, okd = zin && y + 1 < ny && vyo;
       long long ce[NC], co[NC], nte[NC], nto[NC];
-      int En[NC];
+      int En[NC], Et[NC];
       bool bad = false;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -267,17 +282,19 @@ __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ ta
         const double de = (okd && ie) ? __ldg(la + 2 * nx + xe) : 0.0, d_o = (okd && io) ? __ldg(la + 2 * nx + xo) : 0.0;
         const double ue = (ym && ie) ? __ldg(vm + xe) : 0.0, uo = (ym && io) ? __ldg(vm + xo) : 0.0;
         const double we = (yp && ie) ? __ldg(vm + 2 * nx + xe) : 0.0, wo = (yp && io) ? __ldg(vm + 2 * nx + xo) : 0.0;
-        int e = max(max(max(fx_exp(ae), fx_exp(ao)), max(fx_exp(be), fx_exp(bo))), max(fx_exp(de), fx_exp(d_o)));
-        e = max(max(e, max(max(fx_exp(ue), fx_exp(uo)), max(fx_exp(we), fx_exp(wo)))), Ec[c]);
+        // plane sum above at the scale of its own three lines
+        const int et = max(max(max(max(fx_exp(ae), fx_exp(ao)), max(fx_exp(be), fx_exp(bo))), max(fx_exp(de), fx_exp(d_o))), kFxMinE);
+        // the step's scale: both plane sums and the two lines beside
+        const int e = max(max(et, Ec[c]), max(max(fx_exp(ue), fx_exp(uo)), max(fx_exp(we), fx_exp(wo))));
         bad |= e > kFxMaxE;
-        const int ds = e - Ec[c];
-        const long long te = (fx_of(ae, e) + fx_of(be, e)) + fx_of(de, e);
-        const long long to = (fx_of(ao, e) + fx_of(bo, e)) + fx_of(d_o, e);
-        ce[c] = (shr_fx(tpe[c], ds) + te) + (fx_of(ue, e) + fx_of(we, e));  // off-line column sums at x
-        co[c] = (shr_fx(tpo[c], ds) + to) + (fx_of(uo, e) + fx_of(wo, e));
+        const long long te = (fx_of(ae, et) + fx_of(be, et)) + fx_of(de, et);
+        const long long to = (fx_of(ao, et) + fx_of(bo, et)) + fx_of(d_o, et);
+        ce[c] = (shr_fx(tpe[c], e - Ec[c]) + shr_fx(te, e - et)) + (fx_of(ue, e) + fx_of(we, e));  // off-line column sums at x
+        co[c] = (shr_fx(tpo[c], e - Ec[c]) + shr_fx(to, e - et)) + (fx_of(uo, e) + fx_of(wo, e));
         nte[c] = te;
         nto[c] = to;
         En[c] = e;
+        Et[c] = et;
       }
       if (__any_sync(kFull, bad)) {  // huge or non-finite values: FP64 from this plane on
         fixed = false;
@@ -287,7 +304,7 @@ __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ ta
       for (int c = 0; c < NC; ++c) {
         tpe[c] = nte[c];
         tpo[c] = nto[c];
-        Ec[c] = En[c];
+        Ec[c] = Et[c];
       }
       double PE[NC], PO[NC];
       {
@@ -425,10 +442,12 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
   }
   if (yy >= ny || z0 >= z1) return;
   const bool ym = yy - 1 >= 0, yp = yy + 1 < ny;
-  // plane sums over y-1..y+1 of planes z0-1 and z0, fixed point at scale Ep
+  // plane sums over y-1..y+1 of planes z0-1 and z0; each plane sum in fixed
+  // point at the scale of its own three lines (e0, e1), so that the result
+  // does not depend on how planes are grouped into blocks
   long long t0[NC], t1[NC];
   double d0[NC], d1[NC];  // the same in FP64 once a warp leaves the fixed point
-  int Ep;
+  int e0, e1;
   bool fixed;
   {
     const double *l = xg + (long)(z0 - 1) * sxy + (long)(yy - 1) * nx;
@@ -436,20 +455,21 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
     int e = row_max_exp<NC>(l, za && ym, nx, lane, 0);
     e = row_max_exp<NC>(l + nx, za, nx, lane, e);
     e = row_max_exp<NC>(l + 2 * nx, za && yp, nx, lane, e);
-    e = row_max_exp<NC>(l + sxy, ym, nx, lane, e);
+    e0 = max(warp_max(e), kFxMinE);
+    e = row_max_exp<NC>(l + sxy, ym, nx, lane, 0);
     e = row_max_exp<NC>(l + sxy + nx, true, nx, lane, e);
     e = row_max_exp<NC>(l + sxy + 2 * nx, yp, nx, lane, e);
-    Ep = max(warp_max(e), kFxMinE);
-    fixed = Ep <= kFxMaxE;
+    e1 = max(warp_max(e), kFxMinE);
+    fixed = e0 <= kFxMaxE && e1 <= kFxMaxE;
     if (fixed) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) t0[c] = t1[c] = 0;
-      row_add_fx<NC>(l, za && ym, nx, lane, Ep, t0);
-      row_add_fx<NC>(l + nx, za, nx, lane, Ep, t0);
-      row_add_fx<NC>(l + 2 * nx, za && yp, nx, lane, Ep, t0);
-      row_add_fx<NC>(l + sxy, ym, nx, lane, Ep, t1);
-      row_add_fx<NC>(l + sxy + nx, true, nx, lane, Ep, t1);
-      row_add_fx<NC>(l + sxy + 2 * nx, yp, nx, lane, Ep, t1);
+      row_add_fx<NC>(l, za && ym, nx, lane, e0, t0);
+      row_add_fx<NC>(l + nx, za, nx, lane, e0, t0);
+      row_add_fx<NC>(l + 2 * nx, za && yp, nx, lane, e0, t0);
+      row_add_fx<NC>(l + sxy, ym, nx, lane, e1, t1);
+      row_add_fx<NC>(l + sxy + nx, true, nx, lane, e1, t1);
+      row_add_fx<NC>(l + sxy + 2 * nx, yp, nx, lane, e1, t1);
     } else {
       tsum<double, NC>(xg, nx, ny, nz, yy, z0 - 1, lane, d0);
       tsum<double, NC>(xg, nx, ny, nz, yy, z0, lane, d1);
@@ -463,34 +483,30 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
       int e = row_max_exp<NC>(l, zin && ym, nx, lane, 0);
       e = row_max_exp<NC>(l + nx, zin, nx, lane, e);
       e = row_max_exp<NC>(l + 2 * nx, zin && yp, nx, lane, e);
-      const int E = max(warp_max(e), Ep);
-      if (E > kFxMaxE) {  // huge or non-finite values: FP64 from here on
+      const int e2 = max(warp_max(e), kFxMinE);
+      if (e2 > kFxMaxE) {  // huge or non-finite values: FP64 from here on
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          d0[c] = fx_to_double(t0[c], Ep);
-          d1[c] = fx_to_double(t1[c], Ep);
+          d0[c] = fx_to_double(t0[c], e0);
+          d1[c] = fx_to_double(t1[c], e1);
         }
         fixed = false;
       } else {
-        const unsigned ds = (unsigned)(E - Ep);
+        const int E = max(max(e0, e1), e2);
         long long u[NC], t2[NC], ul[NC], ur[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const long long a = ds < 64 ? t0[c] >> ds : (t0[c] < 0 ? -1LL : 0LL);
-          const long long bb = ds < 64 ? t1[c] >> ds : (t1[c] < 0 ? -1LL : 0LL);
-          u[c] = a + bb;
-          t0[c] = bb;
-          t2[c] = 0;
-        }
-        row_add_fx<NC>(l, zin && ym, nx, lane, E, t2);
-        row_add_fx<NC>(l + nx, zin, nx, lane, E, t2);
-        row_add_fx<NC>(l + 2 * nx, zin && yp, nx, lane, E, t2);
+        for (int c = 0; c < NC; ++c) t2[c] = 0;
+        row_add_fx<NC>(l, zin && ym, nx, lane, e2, t2);
+        row_add_fx<NC>(l + nx, zin, nx, lane, e2, t2);
+        row_add_fx<NC>(l + 2 * nx, zin && yp, nx, lane, e2, t2);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          u[c] += t2[c];
+          u[c] = (shr_fx(t0[c], E - e0) + shr_fx(t1[c], E - e1)) + shr_fx(t2[c], E - e2);
+          t0[c] = t1[c];
           t1[c] = t2[c];
         }
-        Ep = E;
+        e0 = e1;
+        e1 = e2;
         line_neighbours_i<NC>(u, ul, ur, lane);
 #pragma unroll
         for (int c = 0; c < NC; ++c) S[c] = fx_to_double((ul[c] + u[c]) + ur[c], E);

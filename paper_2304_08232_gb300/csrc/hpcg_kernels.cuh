@@ -194,9 +194,11 @@ __global__ void k_convert(const Inst *__restrict__ tab, int count, const Tin *__
 // a fixed strided subset, blocks reduce by a fixed tree, and the final sum over
 // block partials runs in a fixed order.
 
-// partials[b] = sum over this block's subset of a_i * b_i
+// partials[b] = sum over this block's subset of a_i * b_i (b in FP64, or the
+// FP32 output of the mixed-precision preconditioner, widened exactly)
+template <typename TB>
 __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const Inst *__restrict__ tab, int count, const double *__restrict__ a,
-                                                             const double *__restrict__ bv, double *__restrict__ partials,
+                                                             const TB *__restrict__ bv, double *__restrict__ partials,
                                                              const CgState *__restrict__ st) {
   pdl_enter();
   __shared__ double sh[kRedThreads / 32];
@@ -206,7 +208,8 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const Inst *__restr
   double s = 0.0;
   if (!(st && st[ii].done)) {
     const long stride = (long)g.nred * kRedThreads;
-    for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) s += a[g.off + i] * bv[g.off + i];
+    #pragma unroll 4
+    for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) s += a[g.off + i] * (double)bv[g.off + i];
   }
   s = block_sum(s, sh);
   if (threadIdx.x == 0) partials[blk] = s;
@@ -252,8 +255,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const Inst *__restrict
   fin_apply<Kind>(st[ii], s, hist ? hist + (long)ii * kHistoryCap : nullptr);
 }
 
-// p = z + beta p (p = z on the first iteration or after a restart)
-__global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict__ tab, int count, const double *__restrict__ zv,
+// p = z + beta p (p = z on the first iteration or after a restart); z in FP64
+// or the FP32 preconditioner output (widened exactly)
+template <typename TZ>
+__global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict__ tab, int count, const TZ *__restrict__ zv,
                                                           double *__restrict__ p, const CgState *__restrict__ st) {
   pdl_enter();
   const int blk = blockIdx.x;
@@ -264,9 +269,11 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict
   const bool first = c.first;
   const double beta = c.beta;
   const long stride = (long)g.nred * kRedThreads;
+  #pragma unroll 4
   for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
     const long gi = g.off + i;
-    p[gi] = first ? zv[gi] : zv[gi] + beta * p[gi];
+    const double zi = (double)zv[gi];
+    p[gi] = first ? zi : zi + beta * p[gi];
   }
 }
 
@@ -285,6 +292,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(const Inst *__restric
   if (!c.done) {
     const double alpha = c.alpha;
     const long stride = (long)g.nred * kRedThreads;
+    #pragma unroll 4
     for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
       const long gi = g.off + i;
       x[gi] = x[gi] + alpha * p[gi];

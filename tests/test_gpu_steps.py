@@ -154,3 +154,28 @@ def test_autotune_keeps_results():
     assert all(v >= 1 for v in shapes)
     z2 = host(g.mg_vcycle(r))
     np.testing.assert_array_equal(z1, z2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_results_independent_of_launch_shape(precision):
+    """Launch shapes only group lines into blocks: SpMV, V-cycle and CG
+    results must be bit-identical for any shape (the tuner's choice varies
+    from run to run)."""
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    dims = (96, 64, 80)
+    n = int(np.prod(dims))
+    shapes_a = [[1, 1, 1, 1], [2, 3, 1, 2], [4, 5, 2, 1], [8, 2, 8, 3]]
+    shapes_b = [[8, 16, 4, 4], [1, 1, 8, 1], [2, 7, 1, 5], [1, 9, 2, 2]]
+    ga = HpcgProblem(*dims, levels=4, precision=precision)
+    gb = HpcgProblem(*dims, levels=4, precision=precision)
+    ga.set_launch_shapes(shapes_a)
+    gb.set_launch_shapes(shapes_b)
+    x = dev(normal(n, 21))
+    np.testing.assert_array_equal(host(ga.spmv(x)), host(gb.spmv(x)))
+    np.testing.assert_array_equal(host(ga.mg_vcycle(x)), host(gb.mg_vcycle(x)))
+    b = ga.get_rhs()
+    xa, sa = ga.pcg_solve(b, max_iters=12, tol=0.0)
+    xb, sb = gb.pcg_solve(b, max_iters=12, tol=0.0)
+    np.testing.assert_array_equal(np.asarray(sa.history), np.asarray(sb.history))
+    np.testing.assert_array_equal(host(xa), host(xb))
