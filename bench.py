@@ -123,6 +123,20 @@ def dist_env():
     return world, rank, local
 
 
+def time_breakdown(prob, b):
+    """Per-level time of one CG iteration, as the paper's Figs. 4-7 (smoother
+    vs restriction/refinement per level, MG vs CG): kernels launched one by one
+    with CUDA events between kernel groups (hpcg_profile_iteration)."""
+    r = prob.profile_iteration(b)
+    tot = r["total_ms"]
+    mg = sum(r["smoother_ms"]) + sum(r["restriction_ms"]) + sum(r["refinement_ms"]) + r["persistent_coarse_ms"] \
+        + r["convert_ms"]
+    r["share"] = {"mg": mg / tot, "cg": 1 - mg / tot, "smoother": sum(r["smoother_ms"]) / tot,
+                  "smoother_per_level": [v / tot for v in r["smoother_ms"]],
+                  "transfer_per_level": [(a + c) / tot for a, c in zip(r["restriction_ms"], r["refinement_ms"])]}
+    return r
+
+
 def persistent_first(prob):
     import ctypes
     from paper_2304_08232_gb300 import _lib
@@ -424,6 +438,8 @@ def run_gpu(args):
     mixed_vs["mixed_vs_fp64_x"] = float((res["mixed"]["x"] - res["fp64"]["x"]).abs().max() / res["fp64"]["x"].abs().max())
     del res
 
+    breakdown = {"fp64": time_breakdown(prob, b), "mixed": time_breakdown(
+        HpcgProblem(NX, NY, NZ, levels=LEVELS, precision="mixed", device=dev), b)}
     forms = {} if args.skip_forms else other_forms(dev, stream)
 
     # --- end to end through the public API with host buffers
@@ -480,6 +496,7 @@ def run_gpu(args):
         "hbm_peak": {"value": peaks.get("hbm_gbs"), "kind": kind},
         "mixed_vs_fp64_to_1e-9": mixed_vs,
         "spmv": spmv,
+        "iteration_breakdown": breakdown,
         "fp64_solve_variants": variants,
         "forms": forms,
         "e2e": e2e,

@@ -205,6 +205,19 @@ int hpcg_batch_offsets(hpcg_handle h, long *offsets_host);
 int hpcg_pcg_solve_batch(hpcg_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol,
                          hpcg_stats *stats, void *stream);
 
+/* --- per-level time breakdown -------------------------------------------------------------- */
+/* The paper's instrument (Section V-C, Figs. 4-7): time of the smoother and of
+ * restriction/refinement per MG level, and of the CG kernels, for one CG
+ * iteration.  Starts a solve of A x = b from x_dev (two iterations are run:
+ * one warm-up, one timed with CUDA events between kernel groups, launched one
+ * by one rather than as a graph), so x_dev is changed.  ms_host (cap >=
+ * 3*levels + 7 doubles) receives: smoother ms per level (restriction fused into
+ * the smoother's last run counts here), separate restriction ms per level,
+ * refinement ms per level, persistent coarse kernel ms, SpMV ms, dot products
+ * ms, vector updates ms, scalar finalisation ms, precision conversions ms, and
+ * the total.  Synchronises `stream`. */
+int hpcg_profile_iteration(hpcg_handle h, const double *b_dev, double *x_dev, double *ms_host, int cap, void *stream);
+
 /* --- launch-shape autotuner ------------------------------------------------------------ */
 /* Times candidate launch shapes (x-lines per block, z-planes per block) of the
  * SpMV and colour-step line kernels on every level of the handle and keeps the

@@ -57,6 +57,7 @@ SIGNATURES = {
     "hpcg_autotune": (_i, [_vp, ctypes.POINTER(_i), _vp]),
     "hpcg_set_launch_shapes": (_i, [_vp, ctypes.POINTER(_i)]),
     "hpcg_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
+    "hpcg_profile_iteration": (_i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i, _vp]),
     "hpcg_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "hpcg_persistent_levels": (_i, [_vp, ctypes.POINTER(_i)]),
     "hpcg_strerror": (ctypes.c_char_p, [_i]),

@@ -121,6 +121,21 @@ class HpcgProblem:
         buf = (ctypes.c_int * len(flat))(*flat)
         check(self.lib.hpcg_set_launch_shapes(self.h, buf), "hpcg_set_launch_shapes")
 
+    def profile_iteration(self, b, x0=None):
+        """Per-level / per-kernel-class milliseconds of one CG iteration
+        (hpcg_profile_iteration); x0 is left untouched (a copy is iterated)."""
+        _need(b, self.n, name="b")
+        x = x0.clone() if x0 is not None else torch.zeros_like(b)
+        L = self.levels
+        buf = (ctypes.c_double * (3 * L + 7))()
+        check(self.lib.hpcg_profile_iteration(self.h, _ptr(b), _ptr(x), buf, 3 * L + 7, _stream()),
+              "hpcg_profile_iteration")
+        v = list(buf)
+        return {"smoother_ms": v[0:L], "restriction_ms": v[L:2 * L], "refinement_ms": v[2 * L:3 * L],
+                "persistent_coarse_ms": v[3 * L], "spmv_ms": v[3 * L + 1], "dot_ms": v[3 * L + 2],
+                "update_ms": v[3 * L + 3], "finalize_ms": v[3 * L + 4], "convert_ms": v[3 * L + 5],
+                "total_ms": v[3 * L + 6]}
+
     def set_kappa(self, kappa):
         if kappa is not None:
             kappa = _need(kappa, self.n, name="kappa")

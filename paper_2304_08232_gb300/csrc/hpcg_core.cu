@@ -26,6 +26,25 @@ using namespace hpcg;
 // inputs only after the predecessor has finished.
 static thread_local bool t_pdl = true;  // set per call from the handle's option
 
+// Per-phase timing of one CG iteration (hpcg_profile_iteration): an event is
+// recorded after every kernel group; the time between two events belongs to
+// the group the later one closes.  Outside a profiling call prof_mark is a no-op.
+enum ProfKind { PK_SMOOTH = 0, PK_RESTRICT, PK_PROLONG, PK_TAIL, PK_SPMV, PK_DOT, PK_UPDATE, PK_FINALIZE, PK_CONVERT, PK_COUNT };
+struct Prof {
+  cudaStream_t s;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> tag;  // kind * 16 + level
+};
+static thread_local Prof *t_prof = nullptr;
+static void prof_mark(int kind, int level) {
+  if (!t_prof) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, t_prof->s);
+  t_prof->ev.push_back(e);
+  t_prof->tag.push_back(kind * 16 + level);
+}
+
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
   cudaLaunchConfig_t cfg = {};
@@ -565,6 +584,7 @@ static int enqueue_smoother(hpcg_ctx *h, int l, const T *r, T *z, int sweeps, cu
       if (fused) *fused = true;
     }
     TRY(enqueue_line_steps<T>(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, z, s, st, vmask, rc_here));
+    prof_mark(PK_SMOOTH, l);
     vmask |= 1 << cls;
     i = j;
   }
@@ -613,6 +633,7 @@ static int enqueue_restrict(hpcg_ctx *h, int l, const T *r, const T *z, T *rc, c
   launch_k(k_restrict_residual<T>, C.tab.nblk_full, dim3(kTileX, kTileY), 0, s, F.tab.inst, C.tab.inst, h->count, r, z, rc,
                                                                           kap_of<T>(F, h->has_kappa), st);
   CKL("k_restrict_residual");
+  prof_mark(PK_RESTRICT, l);
   return HPCG_OK;
 }
 
@@ -621,6 +642,7 @@ static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s
   const LevelData &F = h->lv[l], &C = h->lv[l + 1];
   launch_k(k_prolong_add<T>, C.tab.nblk_full, dim3(kTileX, kTileY), 0, s, F.tab.inst, C.tab.inst, h->count, zc, z, st);
   CKL("k_prolong_add");
+  prof_mark(PK_PROLONG, l);
   return HPCG_OK;
 }
 
@@ -637,6 +659,7 @@ static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_
       if (!fused) TRY(enqueue_restrict<T>(h, l, rl[l], zl[l], rl[l + 1], s, st));
     }
     TRY(enqueue_tail<T>(h, s, st));  // levels first..L-1 and back up to `first`
+    prof_mark(PK_TAIL, first);
     for (int l = first - 1; l >= 0; --l) {
       TRY(enqueue_prolong<T>(h, l, zl[l + 1], zl[l], s, st));
       TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], h->opt.post_sweeps, s, st));
@@ -669,6 +692,7 @@ static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t 
     if (!r32_current) {
       launch_k(k_convert<double, float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, r, L0.r32, st);
       CKL("k_convert");
+      prof_mark(PK_CONVERT, 0);
     }
     float *rl[kMaxLevels], *zl[kMaxLevels];
     for (int l = 0; l < h->levels; ++l) {
@@ -679,6 +703,7 @@ static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t 
     if (!keep_z32) {
       launch_k(k_convert<float, double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, L0.z32, z, st);
       CKL("k_convert");
+      prof_mark(PK_CONVERT, 0);
     }
     return HPCG_OK;
   }
@@ -732,6 +757,7 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   if (mixed) {
     launch_k(k_restart_residual, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, x, b, h->cg_r, L0.r32, kap, h->st);
     CKL("k_restart_residual");
+    prof_mark(PK_UPDATE, 0);
   }
   // z = M r; mixed precision leaves z in FP32 (level-0 z32), which the dot and
   // the p update read directly (r32 is kept current by the CG updates)
@@ -743,21 +769,28 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
     launch_k(k_dot_partial<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, (const double *)h->cg_z, h->part,
              h->st);
   CKL("k_dot_partial");
+  prof_mark(PK_DOT, 0);
   launch_k(k_finalize<FIN_RTZ>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<RTZ>");
+  prof_mark(PK_FINALIZE, 0);
   if (mixed)
     launch_k(k_update_p<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const float *)L0.z32, h->cg_p, h->st);
   else
     launch_k(k_update_p<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_z, h->cg_p, h->st);
   CKL("k_update_p");
+  prof_mark(PK_UPDATE, 0);
   TRY((enqueue_spmv<double, 0>(h, 0, h->cg_p, nullptr, h->cg_ap, kap, h->part, h->st, s)));  // Ap, p.Ap partials
+  prof_mark(PK_SPMV, 0);
   launch_k(k_finalize<FIN_PAP>, h->count, kFinThreads, 0, s, L0.tab.inst, h->count, h->part, L0.tab.nch ? 2 : 1, h->st, h->hist, nullptr);
   CKL("k_finalize<PAP>");
+  prof_mark(PK_FINALIZE, 0);
   launch_k(k_update_xr, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r,
            mixed ? L0.r32 : nullptr, h->part, h->st);
   CKL("k_update_xr");
+  prof_mark(PK_UPDATE, 0);
   launch_k(k_finalize<FIN_NORM>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
   CKL("k_finalize<NORM>");
+  prof_mark(PK_FINALIZE, 0);
   return HPCG_OK;
 }
 
@@ -995,6 +1028,53 @@ static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // C ABI
 extern "C" {
+
+int hpcg_profile_iteration(hpcg_handle h, const double *b_dev, double *x_dev, double *ms_host, int cap, void *stream) {
+  if (!h || !b_dev || !x_dev || !ms_host) return HPCG_ERR_INVALID_ARG;
+  const int L = h->levels;
+  if (cap < 3 * L + 7) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  TRY(reset_error_word(h, s));
+  TRY(enqueue_pcg_init(h, b_dev, x_dev, 2, 0.0, s));
+  // one warm-up iteration (caches, clocks), then the timed one
+  TRY(enqueue_pcg_iter(h, b_dev, x_dev, s));
+  Prof prof;
+  prof.s = s;
+  t_prof = &prof;
+  prof_mark(PK_COUNT, 0);  // start
+  int rc = enqueue_pcg_iter(h, b_dev, x_dev, s);
+  t_prof = nullptr;
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (int i = 0; i < 3 * L + 7; ++i) ms_host[i] = 0.0;
+  if (rc == HPCG_OK && e == cudaSuccess) {
+    for (size_t i = 1; i < prof.ev.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, prof.ev[i - 1], prof.ev[i]);
+      const int kind = prof.tag[i] / 16, lev = prof.tag[i] % 16;
+      double *slot = nullptr;
+      switch (kind) {
+        case PK_SMOOTH: slot = &ms_host[lev]; break;
+        case PK_RESTRICT: slot = &ms_host[L + lev]; break;
+        case PK_PROLONG: slot = &ms_host[2 * L + lev]; break;
+        case PK_TAIL: slot = &ms_host[3 * L]; break;
+        case PK_SPMV: slot = &ms_host[3 * L + 1]; break;
+        case PK_DOT: slot = &ms_host[3 * L + 2]; break;
+        case PK_UPDATE: slot = &ms_host[3 * L + 3]; break;
+        case PK_FINALIZE: slot = &ms_host[3 * L + 4]; break;
+        case PK_CONVERT: slot = &ms_host[3 * L + 5]; break;
+        default: break;
+      }
+      if (slot) *slot += ms;
+      ms_host[3 * L + 6] += ms;
+    }
+  }
+  for (cudaEvent_t ev : prof.ev) cudaEventDestroy(ev);
+  if (rc != HPCG_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "profile synchronize");
+  return HPCG_OK;
+}
 
 int hpcg_set_wait_limit(hpcg_handle h, long long cycles) {
   if (!h || cycles < 0) return HPCG_ERR_INVALID_ARG;

@@ -138,3 +138,28 @@ def test_full_size_vcycle_and_pcg(big):
     xr, hr = o.pcg(o.rhs(), max_iters=3, tol=0.0)
     _history_close(st.history, hr)
     assert normwise(host(x), xr) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_profile_iteration_breakdown(precision):
+    """hpcg_profile_iteration: two CG iterations from x0 with per-level times;
+    the iterate it leaves equals two iterations of the solver."""
+    import ctypes
+    from paper_2304_08232_gb300 import HpcgProblem, _lib
+    need_gpu()
+    g = HpcgProblem(32, 32, 32, levels=4, precision=precision)
+    b = g.get_rhs()
+    r = g.profile_iteration(b)
+    assert all(v >= 0 for v in r["smoother_ms"]) and r["smoother_ms"][0] > 0
+    assert r["spmv_ms"] > 0 and r["total_ms"] > 0
+    parts = sum(r["smoother_ms"]) + sum(r["restriction_ms"]) + sum(r["refinement_ms"]) + r["persistent_coarse_ms"] \
+        + r["spmv_ms"] + r["dot_ms"] + r["update_ms"] + r["finalize_ms"] + r["convert_ms"]
+    assert abs(parts - r["total_ms"]) <= 1e-6 * max(r["total_ms"], 1e-3) + 1e-9
+    lib = _lib.load()
+    x = torch.zeros_like(b)
+    buf = (ctypes.c_double * (3 * 4 + 7))()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.hpcg_profile_iteration(g.h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), buf, 19, s) == 0
+    x2, _ = g.pcg_solve(b, max_iters=2, tol=0.0)
+    np.testing.assert_array_equal(host(x), host(x2))
+    assert lib.hpcg_profile_iteration(g.h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), buf, 5, s) == 1
