@@ -357,23 +357,33 @@ def run_gpu(args):
     sweep_ms = k0.elapsed_time(k1) / reps
     launches_per_sweep = 7
     k_ms = sweep_ms / launches_per_sweep
-    # FP64 instructions per x on the updated lines of one run.  The default
-    # kernel (k_gs_lines_fx) sums the 24 off-line neighbours exactly in 64-bit
-    # fixed point on the integer pipe; its FP64 work per x is the conversion of
-    # that sum (1) + 4 per colour step (3 additions, 1 multiply by 1/A_ii):
-    # 5 for a two-step run, 7 for the three-step run [6,7,6].
-    ops_sweep = (n // 4) * (6 * (1 + 2 * 2) + (1 + 2 * 3))
-    achieved = ops_sweep / (sweep_ms * 1e-3) / 1e9
+    # Roofline of the colour-pair kernel k_gs_lines_fx.  Per launch it must read
+    # z of every line (8 n bytes: the off-line neighbours of a class are the
+    # other three classes, plus its own line), r of its class lines (2 n) and
+    # write z of its class lines (2 n): 12 n bytes.  Its FP64 work is the colour
+    # update, 4 instructions (3 additions, 1 multiply by 1/A_ii) per updated
+    # row; the 24 off-line neighbour sums run exactly in fixed point on the
+    # integer pipe.  Speed of light at 192^3: 12 n / HBM = 12.5 us against
+    # 30 n/4 FP64 instructions / 629 G/s = 8.4 us, so HBM bounds it.
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+    ops_sweep = (n // 4) * (6 * 4 + 4 * 1.5)  # six two-step runs, one three-step run [6,7,6]
+    fp64_rate = ops_sweep / (sweep_ms * 1e-3) / 1e9
     peak_nominal = 152 * 2 * 2070e6 / 1e9  # FP64 instructions per second (2 per SM per clock)
-    bytes_launch = 12 * n  # z of every line read once, r and z of the class lines read/written
-    roofline = {"bound": "alu", "kernel": "k_gs_lines_fx<3> (finest level, colour-pair runs of a symmetric sweep)",
-                "achieved": achieved, "peak": peak_nominal, "unit": "G FP64 instr/s", "frac": achieved / peak_nominal,
-                "peak_basis": "152 SMs x 2 FP64 instructions/clk x 2070 MHz (nominal 1.25 TFLOP/s FMA rate)",
+    bytes_launch = 12 * n
+    achieved_gbs = bytes_launch / (k_ms * 1e-3) / 1e9
+    # DRAM traffic of one launch from the ncu capture of the same kernel on a
+    # 192 x 192 x 512 grid (profiles/k_gs_lines_fx_192x192x512.md), scaled to
+    # 192^3 by the row count (traffic per row is constant)
+    traffic = (189.598464e6 + 21.898240e6) * n / (192 * 192 * 512) if (NX, NY, NZ) == (192, 192, 192) else None
+    roofline = {"bound": "hbm", "kernel": "k_gs_lines_fx<3> (finest level, colour-pair runs of a symmetric sweep)",
+                "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
+                "bytes_algorithmic_per_launch": bytes_launch, "traffic": traffic,
                 "ms_per_launch": k_ms, "ms_per_sweep": sweep_ms, "launches_per_sweep": launches_per_sweep,
-                "fp64_instr_per_sweep": ops_sweep, "hbm_bytes_algorithmic_per_launch": bytes_launch,
-                "hbm_gbs_equivalent": bytes_launch / (k_ms * 1e-3) / 1e9,
-                "hbm_frac_of_measured": bytes_launch / (k_ms * 1e-3) / 1e9 / measured_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS),
-                "traffic": None,
+                "fp64": {"instr_per_sweep": ops_sweep, "g_instr_s": fp64_rate, "peak_g_instr_s": peak_nominal,
+                         "frac": fp64_rate / peak_nominal,
+                         "peak_basis": "152 SMs x 2 FP64 instructions/clk x 2070 MHz"},
                 "launch_shapes_per_level": shapes}
     # SpMV line kernel (secondary): 7 + 4/zc FP64 instructions per row
     zr = shapes[0][1]
@@ -388,10 +398,10 @@ def run_gpu(args):
     k1.record(stream)
     torch.cuda.synchronize()
     sp_ms = k0.elapsed_time(k1) / reps
-    # k_spmv_lines_fx: the 27-point box sum in fixed point; FP64 per row = its
-    # conversion + one FMA (27 x - S)
-    spmv = {"kernel": "k_spmv_lines_fx<6,0>", "ms": sp_ms, "fp64_instr_per_row": 2,
-            "g_fp64_instr_s": n * 2 / (sp_ms * 1e-3) / 1e9,
+    # k_spmv_lines_fx: the 27-point box sum in fixed point; FP64 per row: one
+    # FMA (27 x - S)
+    spmv = {"kernel": "k_spmv_lines_fx<6,0>", "ms": sp_ms, "fp64_instr_per_row": 1,
+            "g_fp64_instr_s": n * 1 / (sp_ms * 1e-3) / 1e9,
             "hbm_gbs_algorithmic": 16 * n / (sp_ms * 1e-3) / 1e9,
             "hbm_frac_of_measured": 16 * n / (sp_ms * 1e-3) / 1e9 / measured_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS)}
     del xs_, ys_
@@ -477,7 +487,6 @@ def run_gpu(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
-    peaks, kind = measured_peaks()
     line = {
         "metric": "HPCG-rule GFLOP/s at 192^3 (FP64 MG-PCG); mixed vs FP64 time to 1e-9",
         "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -493,7 +502,7 @@ def run_gpu(args):
         "max_abs_err_vs_ones": err_ones,
         "gpu_launches": launches,
         "roofline": roofline,
-        "hbm_peak": {"value": peaks.get("hbm_gbs"), "kind": kind},
+        "hbm_peak": {"value": peaks.get("hbm_gbs"), "kind": peak_kind},
         "mixed_vs_fp64_to_1e-9": mixed_vs,
         "spmv": spmv,
         "iteration_breakdown": breakdown,
