@@ -219,6 +219,12 @@ void orc_export_row_nnz(const orc_problem *p, int l, int *out) {
 }
 /* f2c of level l maps level l+1 rows to level l rows; l must not be the coarsest */
 void orc_export_f2c(const orc_problem *p, int l, int *out) { memcpy(out, p->lv[l].f2c, sizeof(int) * p->lv[l + 1].n); }
+/* The right-hand side (which = 0) or result (which = 1) that the last orc_mg
+ * call left on coarse level l >= 1: the restricted residual r_c that Listing 1
+ * hands to the coarser level, and the z_c that level returned. */
+void orc_export_coarse(const orc_problem *p, int l, int which, double *out) {
+  memcpy(out, which ? p->lv[l].z : p->lv[l].r, sizeof(double) * p->lv[l].n);
+}
 
 /* ------------------------------------------------------------------------ */
 /* spmv / mxv (Section II-C): y_i = sum_j A_ij x_j, left to right over the

@@ -15,18 +15,27 @@ def lib_path():
     return os.path.join(_OUT_DIR, "libhpcg_oracle.so")
 
 
+def compile_source(src, out):
+    """Compiles an oracle source file (no FMA contraction, one thread) to a shared library."""
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, src, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, out)
+    return out
+
+
+def source_path():
+    return _SRC
+
+
 def build_oracle(force=False):
     """Compile the oracle with gcc (no FMA contraction, one thread)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     out = lib_path()
     if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
         return out
-    tmp = out + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.check_call(cmd)
-    os.replace(tmp, out)
-    return out
+    return compile_source(_SRC, out)
 
 
 _d = ctypes.POINTER(ctypes.c_double)
@@ -35,11 +44,22 @@ _l = ctypes.POINTER(ctypes.c_long)
 _vp = ctypes.c_void_p
 
 
+def load_library(path):
+    """Loads a compiled oracle library and declares its functions."""
+    lib = ctypes.CDLL(path)
+    _declare(lib)
+    return lib
+
+
 def _load():
     global _LIB
     if _LIB is not None:
         return _LIB
-    lib = ctypes.CDLL(build_oracle())
+    _LIB = load_library(build_oracle())
+    return _LIB
+
+
+def _declare(lib):
     lib.orc_create.restype = _vp
     lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d]
     lib.orc_free.argtypes = [_vp]
@@ -55,6 +75,7 @@ def _load():
     for f in ("orc_export_colors", "orc_export_row_nnz", "orc_export_f2c"):
         getattr(lib, f).argtypes = [_vp, ctypes.c_int, _i]
     lib.orc_export_diag.argtypes = [_vp, ctypes.c_int, _d]
+    lib.orc_export_coarse.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _d]
     lib.orc_spmv.argtypes = [_vp, ctypes.c_int, _d, _d]
     lib.orc_spmv_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, ctypes.c_long, _l, _d, _d]
     lib.orc_row_entries.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, ctypes.c_long, _i, _d]
@@ -65,8 +86,6 @@ def _load():
     lib.orc_mg.argtypes = [_vp, ctypes.c_int, _d, _d]
     lib.orc_mg_apply.argtypes = [_vp, _d, _d]
     lib.orc_pcg.argtypes = [_vp, _d, _d, ctypes.c_int, ctypes.c_double, ctypes.c_int, _d]
-    _LIB = lib
-    return lib
 
 
 def _pd(a):
@@ -80,8 +99,8 @@ def _f64(a):
 class OracleProblem:
     """The HPCG hierarchy of one grid, built by the C oracle."""
 
-    def __init__(self, nx, ny, nz, levels=4, kappa=None, symmetric=True):
-        self.lib = _load()
+    def __init__(self, nx, ny, nz, levels=4, kappa=None, symmetric=True, lib=None):
+        self.lib = lib if lib is not None else _load()
         self.kappa = None if kappa is None else _f64(kappa).copy()
         self.h = self.lib.orc_create(nx, ny, nz, levels, _pd(self.kappa) if self.kappa is not None else None)
         if not self.h:
@@ -182,6 +201,15 @@ class OracleProblem:
         z = np.zeros(self.n(l)) if z0 is None else _f64(z0).copy()
         self.lib.orc_mg(self.h, l, _pd(r), _pd(z))
         return z
+
+    def coarse_state(self, l):
+        """(r_c, z_c) that the last mg call left on coarse level l >= 1."""
+        if not 1 <= l < self.levels:
+            raise ValueError("coarse level out of range")
+        r, z = np.zeros(self.n(l)), np.zeros(self.n(l))
+        self.lib.orc_export_coarse(self.h, l, 0, _pd(r))
+        self.lib.orc_export_coarse(self.h, l, 1, _pd(z))
+        return r, z
 
     def pcg(self, b, x0=None, max_iters=50, tol=0.0, precond=True):
         b = _f64(b)

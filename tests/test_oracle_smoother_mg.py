@@ -111,3 +111,55 @@ def test_vcycle_is_linear():
     lhs = p.mg(2.0 * a - 3.0 * b)
     rhs = 2.0 * p.mg(a) - 3.0 * p.mg(b)
     np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-12 * np.abs(rhs).max())
+
+
+def _dense_smooth(A, cols, r, z, symmetric):
+    z = D.gs_forward_sorted(A, cols, r, z)
+    return D.gs_backward_sorted(A, cols, r, z) if symmetric else z
+
+
+@pytest.mark.parametrize("kappa_seed", [None, 22])
+def test_coarse_levels_receive_listing1_inputs(kappa_seed):
+    """Every coarse level gets r_c = R (r - A z) after the pre-smoother and starts
+    from z_c = 0, also on a second call whose buffers hold the first call's
+    values.  The forward-only sweep is used: with it the restricted residual is
+    of the order of the residual itself (see the next test for why the
+    symmetric sweep leaves only rounding there)."""
+    kappa = None if kappa_seed is None else np.random.default_rng(kappa_seed).uniform(0, 1, 512)
+    p = OracleProblem(8, 8, 8, levels=3, kappa=kappa, symmetric=False)
+    As = [p.csr(l).toarray() for l in range(3)]
+    cols = [p.colors(l) for l in range(3)]
+    Rs = [D.injection_matrix(p.n(l), p.f2c(l)) for l in range(2)]
+    p.mg(_rand(p.n(), 23))  # leaves stale values on every coarse level
+    r = _rand(p.n(), 24)
+    p.mg(r)
+    for l in range(1, 3):
+        z = _dense_smooth(As[l - 1], cols[l - 1], r, np.zeros(p.n(l - 1)), False)
+        rc = Rs[l - 1] @ (r - As[l - 1] @ z)
+        rc_o, zc_o = p.coarse_state(l)
+        assert np.abs(rc).max() > 0.1 * np.abs(r - As[l - 1] @ z).max()
+        np.testing.assert_allclose(rc_o, rc, rtol=0, atol=1e-12 * np.abs(rc).max())
+        zc = D.dense_vcycle(As[l:], cols[l:], Rs[l:], rc, symmetric=False)
+        np.testing.assert_allclose(zc_o, zc, rtol=0, atol=1e-12 * np.abs(zc).max())
+        r = rc
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_vcycle_equals_two_fine_sweeps(symmetric):
+    """A property of Listing 1 with this smoother and injection, not of the code:
+    refinement writes only the all-even points, which form colour 0, and the
+    post-smoother starts by recomputing colour 0 from its neighbours alone, so
+    the coarse correction is overwritten (up to rounding); with the symmetric
+    sweep the restricted residual is itself rounding, because the pre-smoother
+    ends with colour 0."""
+    p = OracleProblem(16, 16, 16, levels=4, symmetric=symmetric)
+    r = _rand(p.n(), 25)
+    z = p.mg(r)
+    z2 = p.rbgs(r, p.rbgs(r, np.zeros(p.n())))
+    assert np.abs(z - z2).max() <= 1e-14 * np.abs(z).max()
+    rc, zc = p.coarse_state(1)
+    res = np.abs(r - p.spmv(p.rbgs(r, np.zeros(p.n())))).max()
+    if symmetric:
+        assert np.abs(rc).max() <= 1e-13 * res
+    else:
+        assert np.abs(rc).max() > 0.1 * res and np.abs(zc).max() > 0
