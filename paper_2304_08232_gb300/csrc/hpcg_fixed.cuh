@@ -17,7 +17,10 @@
 // values below 2^-1016 in magnitude count as zero (an absolute error under
 // 1e-305); a warp whose step holds huge (E > 2000) or non-finite values
 // continues with FP64 sums, so NaN and Inf still propagate.  The colour-step
-// update itself (r + sum) / A_ii stays in FP64.
+// update (r + sum) / A_ii stays in FP64 (on this GPU the integer pipe, not
+// the FP64 pipe, limits these kernels).  Without kappa the SpMV's 27 x - S is
+// formed in fixed point too: its only rounding is the final conversion, and
+// it issues no FP64 instruction.
 #pragma once
 #include "hpcg_lines.cuh"
 
@@ -112,16 +115,11 @@ __device__ __forceinline__ int max_exp3(const double (&a)[NC], const double (&b)
   return m;
 }
 
-// Colour steps along the own line (FP64), the stores, and the fused
-// residual + injection: the part of k_gs_lines after the off-line sums.
+// The own line's values (E_ at even x, O_ at odd x; zero where the line holds
+// no valid data yet) and the right-hand side there.
 template <int NC>
-__device__ __forceinline__ void pair_update(const Inst &g, int ii, int zz, int y, int lane, int pa, int steps, bool own_valid,
-                                            const double (&PE)[NC], const double (&PO)[NC], const double *__restrict__ rg,
-                                            double *__restrict__ zg, const double *__restrict__ invd, const Inst *__restrict__ tabc,
-                                            double *__restrict__ rc, const double *__restrict__ kap) {
-  const int nx = g.nx;
-  const long rowbase = (long)zz * nx * g.ny + (long)y * nx;
-  double E_[NC], O_[NC], rE[NC], rO[NC];
+__device__ __forceinline__ void load_own(const double *__restrict__ zg, const double *__restrict__ rg, long rowbase, int nx, int lane,
+                                         bool own_valid, double (&E_)[NC], double (&O_)[NC], double (&rE)[NC], double (&rO)[NC]) {
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const int xe = 2 * (lane + 32 * c), xo = xe + 1;
@@ -130,6 +128,19 @@ __device__ __forceinline__ void pair_update(const Inst &g, int ii, int zz, int y
     rE[c] = xe < nx ? rg[rowbase + xe] : 0.0;
     rO[c] = xo < nx ? rg[rowbase + xo] : 0.0;
   }
+}
+
+// Colour steps along the own line (FP64), the stores, and the fused
+// residual + injection: the part of k_gs_lines after the off-line sums.
+// E_, O_, rE, rO hold the own line as load_own reads it.
+template <int NC>
+__device__ __forceinline__ void pair_steps(const Inst &g, int ii, int zz, int y, int lane, int pa, int steps, bool own_valid,
+                                           const double (&PE)[NC], const double (&PO)[NC], double (&E_)[NC], double (&O_)[NC],
+                                           const double (&rE)[NC], const double (&rO)[NC], double *__restrict__ zg,
+                                           const double *__restrict__ invd, const Inst *__restrict__ tabc, double *__restrict__ rc,
+                                           const double *__restrict__ kap) {
+  const int nx = g.nx;
+  const long rowbase = (long)zz * nx * g.ny + (long)y * nx;
   double nb[NC];
   for (int s = 0; s < steps; ++s) {
     const int q = (s & 1) ? 1 - pa : pa;
@@ -178,8 +189,31 @@ __device__ __forceinline__ void pair_update(const Inst &g, int ii, int zz, int y
   }
 }
 
+template <int NC>
+__device__ __forceinline__ void pair_update(const Inst &g, int ii, int zz, int y, int lane, int pa, int steps, bool own_valid,
+                                            const double (&PE)[NC], const double (&PO)[NC], const double *__restrict__ rg,
+                                            double *__restrict__ zg, const double *__restrict__ invd, const Inst *__restrict__ tabc,
+                                            double *__restrict__ rc, const double *__restrict__ kap) {
+  double E_[NC], O_[NC], rE[NC], rO[NC];
+  load_own<NC>(zg, rg, (long)zz * g.nx * g.ny + (long)y * g.nx, g.nx, lane, own_valid, E_, O_, rE, rO);
+  pair_steps<NC>(g, ii, zz, y, lane, pa, steps, own_valid, PE, PO, E_, O_, rE, rO, zg, invd, tabc, rc, kap);
+}
+
 // Arithmetic right shift that saturates for shifts of 64 or more.
 __device__ __forceinline__ long long shr_fx(long long v, int d) { return d < 64 ? v >> d : (v < 0 ? -1LL : 0LL); }
+
+// ceil(2^68 / 26): for 0 <= a < 2^64, floor(a * kDiv26 / 2^64) equals a * 16/26
+// to within one unit (the multiplier's relative excess is below 2^-63).
+constexpr unsigned long long kDiv26 = 11351842506898185610ULL;
+
+// (s 2^(S-1080)) / 26 as FP64 with one rounding: the quotient keeps four more
+// fraction bits than s (scale S - 4), then converts as fx_to_double does.
+__device__ __forceinline__ double fx_div26(long long s, int S) {
+  const unsigned long long a = s < 0 ? 0ULL - (unsigned long long)s : (unsigned long long)s;
+  const long long q = (long long)__umul64hi(a, kDiv26);
+  return fx_to_double(s < 0 ? -q : q, S - 4);
+}
+
 
 template <int NC>
 __device__ __forceinline__ void prev_of_int(const int (&v)[NC], int (&out)[NC], int lane) {
@@ -306,7 +340,8 @@ __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ ta
         tpo[c] = nto[c];
         Ec[c] = Et[c];
       }
-      double PE[NC], PO[NC];
+      long long PEf[NC], POf[NC];
+      int Ee[NC], Eo[NC];
       {
         long long sh[NC];
         int Es[NC];
@@ -315,17 +350,27 @@ __global__ void __launch_bounds__(256) k_gs_lines_fx(const Inst *__restrict__ ta
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const int E3 = max(Es[c], En[c]);
-          PE[c] = fx_to_double((shr_fx(sh[c], E3 - Es[c]) + shr_fx(ce[c], E3 - En[c])) + shr_fx(co[c], E3 - En[c]), E3);
+          PEf[c] = (shr_fx(sh[c], E3 - Es[c]) + shr_fx(ce[c], E3 - En[c])) + shr_fx(co[c], E3 - En[c]);
+          Ee[c] = E3;
         }
         next_of_i<NC>(ce, sh, lane);  // column x+1 of an odd x
         next_of_int<NC>(En, Es, lane);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const int E3 = max(Es[c], En[c]);
-          PO[c] = fx_to_double((shr_fx(ce[c], E3 - En[c]) + shr_fx(co[c], E3 - En[c])) + shr_fx(sh[c], E3 - Es[c]), E3);
+          POf[c] = (shr_fx(ce[c], E3 - En[c]) + shr_fx(co[c], E3 - En[c])) + shr_fx(sh[c], E3 - Es[c]);
+          Eo[c] = E3;
         }
       }
-      pair_update<NC>(g, ii, zz, y, lane, pa, steps, own_valid, PE, PO, rg, zg, invd, tabc, rc, kap);
+      {
+        double PE[NC], PO[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          PE[c] = fx_to_double(PEf[c], Ee[c]);
+          PO[c] = fx_to_double(POf[c], Eo[c]);
+        }
+        pair_update<NC>(g, ii, zz, y, lane, pa, steps, own_valid, PE, PO, rg, zg, invd, tabc, rc, kap);
+      }
     }
   }
   // FP64 sums for the remaining planes (rare: huge or non-finite values)
@@ -479,6 +524,9 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
     const double *l = xg + (long)(zz + 1) * sxy + (long)(yy - 1) * nx;
     const bool zin = zz + 1 < nz;
     double S[NC];
+    long long Sf[NC];  // the box sums in fixed point at scale SE while the warp stays fixed
+    int SE = 0;
+    bool sfix = false;
     if (fixed) {
       int e = row_max_exp<NC>(l, zin && ym, nx, lane, 0);
       e = row_max_exp<NC>(l + nx, zin, nx, lane, e);
@@ -509,7 +557,9 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
         e1 = e2;
         line_neighbours_i<NC>(u, ul, ur, lane);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) S[c] = fx_to_double((ul[c] + u[c]) + ur[c], E);
+        for (int c = 0; c < NC; ++c) Sf[c] = (ul[c] + u[c]) + ur[c];
+        SE = E;
+        sfix = true;
       }
     }
     if (!fixed) {
@@ -533,8 +583,14 @@ __global__ void __launch_bounds__(256) k_spmv_lines_fx(const Inst *__restrict__ 
       if (xx < nx) {
         const double xi = xg[rowbase + xx];
         const long gi = g.off + rowbase + xx;
-        const double d1 = kap ? 27.0 + kap[gi] : 27.0;
-        const double ax = d1 * xi - S[c];
+        double ax;
+        if (sfix && !kap) {
+          // 27 x - S exactly at scale SE + 1 (|27 x| and |S| < 27 2^57 there), one rounding
+          ax = fx_to_double(27 * fx_of(xi, SE + 1) - (Sf[c] >> 1), SE + 1);
+        } else {
+          const double d1 = kap ? 27.0 + kap[gi] : 27.0;
+          ax = d1 * xi - (sfix ? fx_to_double(Sf[c], SE) : S[c]);
+        }
         const double out = Mode == 0 ? ax : b[gi] - ax;
         y[gi] = out;
         if (partials) dotv += xi * out;
