@@ -77,6 +77,14 @@ typedef struct {
   int persistent;   /* 1: the smallest levels of the V-cycle run in one persistent cooperative
                        kernel (hpcg_persistent_levels); 0 (default): one launch per step, which
                        measured faster on one 192^3 grid (graph launches beat grid barriers) */
+  int block_fp;     /* 1 (default): inside the FP64 V-cycle (with fixed_point, the symmetric
+                       smoother, no persistent kernel, grids up to 384 points along x) the level
+                       vectors z are kept as 64-bit integer mantissas with one exponent per x-line,
+                       so colour steps add exactly without converting each value they load; each
+                       new value is rounded once to about FP64 precision of its line (53 bits for
+                       values of the line's typical size, an absolute 2^-56 of its largest), and
+                       non-finite values end as NaN; r and the result z stay FP64.  0: the FP64
+                       V-cycle keeps z in FP64 */
 } hpcg_options;
 
 typedef struct {

@@ -58,7 +58,8 @@ class HpcgProblem:
     """One grid hierarchy (hpcg_setup_ex) with a torch-allocated workspace."""
 
     def __init__(self, nx, ny, nz, levels=4, precision="fp64", kappa=None, pre_sweeps=1, post_sweeps=1,
-                 symmetric=True, max_rhs=0, check_every=1, persistent=False, fixed_point=True, pdl=True, device=None):
+                 symmetric=True, max_rhs=0, check_every=1, persistent=False, fixed_point=True, pdl=True, block_fp=True,
+                 device=None):
         self.lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("HpcgProblem needs a CUDA device")
@@ -74,6 +75,7 @@ class HpcgProblem:
         opt.persistent = 1 if persistent else 0
         opt.fixed_point = 1 if fixed_point else 0
         opt.pdl = 1 if pdl else 0
+        opt.block_fp = 1 if block_fp else 0
         self.dims = (nx, ny, nz)
         self.levels = levels
         self.precision = precision

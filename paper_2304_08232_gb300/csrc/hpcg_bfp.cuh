@@ -1,0 +1,347 @@
+// hpcg_bfp.cuh -- the FP64 V-cycle with its level vectors z held in block
+// floating point: a 64-bit integer mantissa per point and one exponent per
+// x-line.
+//
+// The colour-pair kernel of hpcg_fixed.cuh spends most of its integer
+// instructions turning the FP64 values it loads into fixed point, about five
+// conversions per updated point.  Here z stays in that form between kernels:
+// point i of line L holds q_i with value q_i 2^(e_L - 1080), |q_i| < 2^58, so
+// that a kernel only aligns whole lines to a common exponent (one shift per
+// value, by an amount that is the same across the warp) before adding them
+// exactly.  Each colour step's sum r + sum_{j != i} z_j is formed exactly at
+// a scale S of the whole line, and the new value costs one rounding: the
+// division by A_ii = 26 through an integer multiplier, or a multiply by
+// 1 / A_ii in FP64 when kappa is set, at scale S - 3 (at least 2^-56 of the
+// step's largest term).  The line is then stored with its exponent lowered
+// until its largest mantissa has bit 57 set (an exact shift), so exponents
+// follow the data from run to run instead of the sums' bounds.
+//
+// Every exponent is a function of the data alone (the lines summed, the
+// right-hand side, the own line), never of how lines and planes are grouped
+// into blocks, so results do not depend on the launch shape.  A line whose
+// values are non-finite or beyond 2^977 gets the exponent kBfpNaN and reads as
+// NaN from then on, so non-finite input still ends in a NaN result.
+//
+// Only the V-cycle uses this form: the right-hand sides r stay FP64, and the
+// finest level's z is written back in FP64 by the last run that touches each
+// line class (the final-touch runs of the last post-smoother).
+#pragma once
+#include "hpcg_fixed.cuh"
+
+namespace hpcg {
+
+constexpr int kBfpNaN = 2047;  // exponent of a line that reads as NaN
+
+// Arithmetic right shift by d >= 0 (amounts of 64 or more give the sign).
+__device__ __forceinline__ long long shr_q(long long v, int d) {
+  long long r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"((unsigned)d));
+  return r;
+}
+
+__device__ __forceinline__ double bfp_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// Mantissa pairs (x = 2k, 2k+1 for k = lane + 32c) of one line; nx is even,
+// so a pair is either inside the line or past its end.
+template <int NC>
+__device__ __forceinline__ void ld_pairs_q(const long long *__restrict__ line, bool ok, int nx, int lane, long long (&e)[NC],
+                                           long long (&o)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int xe = 64 * c + 2 * lane;
+    if (ok && xe < nx) {
+      const longlong2 v = __ldg(reinterpret_cast<const longlong2 *>(line + xe));
+      e[c] = v.x;
+      o[c] = v.y;
+    } else {
+      e[c] = 0;
+      o[c] = 0;
+    }
+  }
+}
+template <int NC>
+__device__ __forceinline__ void ld_pairs_d(const double *__restrict__ line, int nx, int lane, double (&e)[NC], double (&o)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int xe = 64 * c + 2 * lane;
+    if (xe < nx) {
+      const double2 v = __ldg(reinterpret_cast<const double2 *>(line + xe));
+      e[c] = v.x;
+      o[c] = v.y;
+    } else {
+      e[c] = 0.0;
+      o[c] = 0.0;
+    }
+  }
+}
+
+// Sum over lines y-1, y, y+1 of plane zz (those with ok set), at the largest
+// exponent of the three; returns that exponent.
+template <int NC>
+__device__ __forceinline__ int bfp_plane_sum(const long long *__restrict__ qg, const int *__restrict__ eg, int nx, int ny, long sxy, int y,
+                                             int zz, bool oka, bool okb, bool okd, int lane, long long (&te)[NC], long long (&to)[NC]) {
+  const long li = (long)zz * ny + y;
+  const int ea = oka ? __ldg(eg + li - 1) : kFxMinE;
+  const int eb = okb ? __ldg(eg + li) : kFxMinE;
+  const int ed = okd ? __ldg(eg + li + 1) : kFxMinE;
+  const int et = max(max(ea, eb), ed);
+  const long long *la = qg + (long)zz * sxy + (long)(y - 1) * nx;
+  long long ae[NC], ao[NC], be[NC], bo[NC], de[NC], d_o[NC];
+  ld_pairs_q<NC>(la, oka, nx, lane, ae, ao);
+  ld_pairs_q<NC>(la + nx, okb, nx, lane, be, bo);
+  ld_pairs_q<NC>(la + 2 * nx, okd, nx, lane, de, d_o);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    te[c] = (shr_q(ae[c], et - ea) + shr_q(be[c], et - eb)) + shr_q(de[c], et - ed);
+    to[c] = (shr_q(ao[c], et - ea) + shr_q(bo[c], et - eb)) + shr_q(d_o[c], et - ed);
+  }
+  return et;
+}
+
+// New value of a colour step from its exact sum t (scale S), stored at scale
+// sout: t / 26 with four guard bits from the integer multiplier, rounded to
+// nearest at S - 3; with kappa, t * (1 / A_ii) in FP64 converted at sout.
+__device__ __forceinline__ long long bfp_new_value(long long t, int S, int sout, const double *__restrict__ invd, long gi) {
+  if (!invd) {
+    const unsigned long long a = t < 0 ? 0ULL - (unsigned long long)t : (unsigned long long)t;
+    const long long q = (long long)((__umul64hi(a, kDiv26) + 1ULL) >> 1);
+    return t < 0 ? -q : q;
+  }
+  return fx_of(fx_to_double(t, S) * invd[gi], sout);
+}
+
+// Colour-pair runs of the V-cycle on the block-floating-point z (see
+// k_gs_lines / k_gs_lines_fx for the run structure): `steps` >= 2 colour
+// steps on the lines of class (py, pz), x parity pa first.  vmask: classes
+// holding valid z (others read as zero).  rc (nullable): fused residual +
+// injection into the FP64 right-hand side of level l+1 (runs of class (0,0)
+// ending on even x).  zout (nullable): FP64 copy of the updated lines.
+template <int NC>
+__global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
+                                                      int steps, int vmask, const double *__restrict__ r, long long *__restrict__ zq,
+                                                      int *__restrict__ ze, const double *__restrict__ invd, const CgState *__restrict__ st,
+                                                      const Inst *__restrict__ tabc, double *__restrict__ rc,
+                                                      const double *__restrict__ kap, double *__restrict__ zout) {
+  pdl_enter();
+  const int blk = blockIdx.x;
+  const int ii = find_inst<4>(tab, count, blk);
+  const Inst g = tab[ii];
+  if (st && st[ii].done) return;
+  const int cy = (g.ny - py + 1) / 2, cz = (g.nz - pz + 1) / 2;
+  const int nby = (half_up(g.ny) + lpc - 1) / lpc;
+  const int lb = blk - g.blk_line;
+  const int j = (lb % nby) * lpc + threadIdx.y;
+  const int m0 = (lb / nby) * zc;
+  const int m1 = min(m0 + zc, cz);
+  if (j >= cy || m0 >= m1) return;  // whole warp
+  const int lane = threadIdx.x;
+  const int y = 2 * j + py;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long sxy = (long)nx * ny;
+  long long *qg = zq + g.off;
+  int *eg = ze + g.poff;  // exponent of line (y, z) at eg[z ny + y]
+  const double *rg = r + g.off;
+  const bool vy = (vmask >> line_class(y + 1, pz)) & 1;  // lines (y +- 1, z) of the updated planes
+  const bool ym = y - 1 >= 0 && vy, yp = y + 1 < ny && vy;
+  const bool own_valid = (vmask >> line_class(y, pz)) & 1;
+  const bool vyo = (vmask >> line_class(y + 1, pz + 1)) & 1;  // lines (y +- 1, z +- 1)
+  const bool vy0 = (vmask >> line_class(y, pz + 1)) & 1;      // line (y, z +- 1)
+
+  long long tpe[NC], tpo[NC];  // plane sum of the plane below the current one, at exponent Ec
+  int Ec;
+  {
+    const int zz = 2 * m0 + pz - 1;
+    const bool zin = zz >= 0;
+    Ec = bfp_plane_sum<NC>(qg, eg, nx, ny, sxy, y, zz, zin && y - 1 >= 0 && vyo, zin && vy0, zin && y + 1 < ny && vyo, lane, tpe, tpo);
+  }
+  for (int m = m0; m < m1; ++m) {
+    const int zz = 2 * m + pz;
+    const bool zin = zz + 1 < nz;
+    long long te[NC], to[NC];
+    const int et = bfp_plane_sum<NC>(qg, eg, nx, ny, sxy, y, zz + 1, zin && y - 1 >= 0 && vyo, zin && vy0, zin && y + 1 < ny && vyo, lane,
+                                     te, to);
+    const long li = (long)zz * ny + y;
+    const long rowbase = (long)zz * sxy + (long)y * nx;
+    const int eu = ym ? __ldg(eg + li - 1) : kFxMinE;
+    const int ew = yp ? __ldg(eg + li + 1) : kFxMinE;
+    const int eo = own_valid ? eg[li] : kFxMinE;
+    long long ue[NC], uo[NC], we[NC], wo[NC], qe[NC], qo[NC];
+    ld_pairs_q<NC>(qg + rowbase - nx, ym, nx, lane, ue, uo);
+    ld_pairs_q<NC>(qg + rowbase + nx, yp, nx, lane, we, wo);
+    ld_pairs_q<NC>(qg + rowbase, own_valid, nx, lane, qe, qo);
+    double rE[NC], rO[NC];
+    ld_pairs_d<NC>(rg + rowbase, nx, lane, rE, rO);
+    // off-line sums: column sums at x (both planes beside + the two lines beside), then over x-1..x+1
+    const int E = max(max(Ec, et), max(eu, ew));
+    long long PE[NC], PO[NC];
+    {
+      long long ce[NC], co[NC], sh[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        ce[c] = (shr_q(tpe[c], E - Ec) + shr_q(te[c], E - et)) + (shr_q(ue[c], E - eu) + shr_q(we[c], E - ew));
+        co[c] = (shr_q(tpo[c], E - Ec) + shr_q(to[c], E - et)) + (shr_q(uo[c], E - eu) + shr_q(wo[c], E - ew));
+      }
+      prev_of_i<NC>(co, sh, lane);  // column x-1 of an even x
+#pragma unroll
+      for (int c = 0; c < NC; ++c) PE[c] = (sh[c] + ce[c]) + co[c];
+      next_of_i<NC>(ce, sh, lane);  // column x+1 of an odd x
+#pragma unroll
+      for (int c = 0; c < NC; ++c) PO[c] = (ce[c] + co[c]) + sh[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      tpe[c] = te[c];
+      tpo[c] = to[c];
+    }
+    Ec = et;
+    // the scale of the colour steps: every term below 2^56 there (r, the own
+    // line, P whose 24 terms sum below 2^62.6 at E), with 3 more bits per
+    // doubling of |1 / A_ii| above 1/2 (kappa), so that up to three steps of
+    // new values stay below 2^58
+    int er = kFxMinE;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) er = max(er, max(fx_exp(rE[c]), fx_exp(rO[c])));
+    er = warp_max(er);
+    int idx = 0;
+    if (invd) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 64 * c + 2 * lane;
+        if (xe < nx) idx = max(idx, max(fx_exp(invd[g.off + rowbase + xe]), fx_exp(invd[g.off + rowbase + xe + 1])));
+      }
+      idx = warp_max(idx);
+    }
+    const int S = max(E + 5, max(er, eo)) + 2 + 3 * max(0, idx - 1021);
+    const int sout = (invd && idx > 1018) ? S : S - 3;
+    const bool bad = E > kFxMaxE || er > kFxMaxE || eo > kFxMaxE || S > kFxMaxE + 8;  // the same in every lane
+    if (bad) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 64 * c + 2 * lane;
+        if (xe < nx) {
+          *reinterpret_cast<longlong2 *>(qg + rowbase + xe) = make_longlong2(0, 0);
+          if (zout) *reinterpret_cast<double2 *>(zout + g.off + rowbase + xe) = make_double2(bfp_nan(), bfp_nan());
+        }
+      }
+      if (lane == 0) eg[li] = kBfpNaN;
+      if (rc) {
+        const Inst gc = tabc[ii];
+        const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (64 * c + 2 * lane < nx) rc[cbase + 32 * c + lane] = bfp_nan();
+      }
+      continue;
+    }
+    long long re[NC], ro[NC], oE[NC], oO[NC], sE[NC], sO[NC], nb[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      re[c] = fx_of(rE[c], S) + shr_q(PE[c], S - E);
+      ro[c] = fx_of(rO[c], S) + shr_q(PO[c], S - E);
+      oE[c] = shr_q(qe[c], S - eo);
+      oO[c] = shr_q(qo[c], S - eo);
+      sE[c] = 0;
+      sO[c] = 0;
+    }
+    const int down = S - sout;  // 3, or 0 with a large |1 / A_ii|
+    for (int s = 0; s < steps; ++s) {
+      const int q = (s & 1) ? 1 - pa : pa;
+      if (q == 0) {
+        prev_of_i<NC>(oO, nb, lane);  // O at x - 1 of every even x
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int xe = 64 * c + 2 * lane;
+          if (xe < nx) {
+            sE[c] = bfp_new_value((re[c] + nb[c]) + oO[c], S, sout, invd, g.off + rowbase + xe);
+            oE[c] = shr_q(sE[c], down);
+          }
+        }
+      } else {
+        next_of_i<NC>(oE, nb, lane);  // E at x + 1 of every odd x
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int xo = 64 * c + 2 * lane + 1;
+          if (xo < nx) {
+            sO[c] = bfp_new_value((ro[c] + oE[c]) + nb[c], S, sout, invd, g.off + rowbase + xo);
+            oO[c] = shr_q(sO[c], down);
+          }
+        }
+      }
+    }
+    // Stored exponent: the new values are far below the scale bound sout they
+    // were rounded at, so shift them up until the line's largest |q| reaches
+    // bit 57 (exact).  The exponent then follows the data, and the next run's
+    // scales, derived from its neighbours' exponents, stay tight.
+    unsigned long long mag = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      mag |= sE[c] < 0 ? 0ULL - (unsigned long long)sE[c] : (unsigned long long)sE[c];
+      mag |= sO[c] < 0 ? 0ULL - (unsigned long long)sO[c] : (unsigned long long)sO[c];
+    }
+    const unsigned mhi = __reduce_or_sync(kFull, (unsigned)(mag >> 32)), mlo = __reduce_or_sync(kFull, (unsigned)mag);
+    const int lz = mhi ? __clz(mhi) : 32 + __clz(mlo);  // 64 for an all-zero line
+    const int up = min(max(lz - 6, 0), sout - kFxMinE);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int xe = 64 * c + 2 * lane;
+      if (xe < nx) {
+        *reinterpret_cast<longlong2 *>(qg + rowbase + xe) =
+            make_longlong2((long long)((unsigned long long)sE[c] << up), (long long)((unsigned long long)sO[c] << up));
+        if (zout)
+          *reinterpret_cast<double2 *>(zout + g.off + rowbase + xe) = make_double2(fx_to_double(sE[c], sout), fx_to_double(sO[c], sout));
+      }
+    }
+    if (lane == 0) eg[li] = sout - up;
+    if (rc) {  // r - A z at the even points from the final values, exactly
+      const Inst gc = tabc[ii];
+      const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
+      prev_of_i<NC>(oO, nb, lane);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 64 * c + 2 * lane;
+        if (xe < nx) {
+          const long long t = (re[c] + nb[c]) + oO[c];  // r + sum of the neighbours, scale S
+          double res;
+          if (!kap)  // 26 E at scale S - 3 is 13 E at S - 2; t at S is 4 t at S - 2
+            res = fx_to_double(4 * t - 13 * sE[c], S - 2);
+          else
+            res = fx_to_double(t, S) - (26.0 + kap[g.off + rowbase + xe]) * fx_to_double(sE[c], sout);
+          rc[cbase + 32 * c + lane] = res;
+        }
+      }
+    }
+  }
+}
+
+// Refinement z_f <- z_f + R^T z_c on the block-floating-point vectors: one
+// warp per coarse line (yc, zc), which feeds the even points of fine line
+// (2 yc, 2 zc).  The fine line moves to exponent max(e_f, e_c) + 1, which
+// keeps the sums below 2^58.
+__global__ void __launch_bounds__(256) k_prolong_bfp(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count, int nlines,
+                                                     const long long *__restrict__ qc, const int *__restrict__ ec,
+                                                     long long *__restrict__ qf, int *__restrict__ ef, const CgState *__restrict__ st) {
+  pdl_enter();
+  const int wl = blockIdx.x * (blockDim.y) + threadIdx.y;
+  if (wl >= nlines) return;
+  const int ii = find_inst<5>(tabc, count, wl);
+  if (st && st[ii].done) return;
+  const Inst gc = tabc[ii], gf = tabf[ii];
+  const int li = wl - gc.poff;
+  const int yc = li % gc.ny, zc = li / gc.ny;
+  const int yf = 2 * yc, zf = 2 * zc;
+  const long lf = (long)zf * gf.ny + yf;
+  const int e_f = ef[gf.poff + lf], e_c = __ldg(ec + gc.poff + li);
+  const bool bad = e_f > kFxMaxE || e_c > kFxMaxE;
+  const int S = max(e_f, e_c) + 1;
+  long long *fl = qf + gf.off + lf * gf.nx;
+  const long long *cl = qc + gc.off + (long)li * gc.nx;
+  for (int xe = 2 * threadIdx.x; xe < gf.nx; xe += 64) {
+    const longlong2 v = *reinterpret_cast<const longlong2 *>(fl + xe);
+    const long long c = __ldg(cl + (xe >> 1));
+    *reinterpret_cast<longlong2 *>(fl + xe) =
+        bad ? make_longlong2(0, 0) : make_longlong2(shr_q(v.x, S - e_f) + shr_q(c, S - e_c), shr_q(v.y, S - e_f));
+  }
+  if (threadIdx.x == 0) ef[gf.poff + lf] = bad ? kBfpNaN : S;
+}
+
+}  // namespace hpcg

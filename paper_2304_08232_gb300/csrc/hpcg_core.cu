@@ -17,6 +17,7 @@
 #include "hpcg_lines.cuh"
 #include "hpcg_tail.cuh"
 #include "hpcg_fixed.cuh"
+#include "hpcg_bfp.cuh"
 
 using namespace hpcg;
 
@@ -192,6 +193,8 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
       br += g.nred;
     }
     L.n = rows;
+    L.nlines = 0;
+    for (const Inst &g : L.inst) L.nlines += (long)g.ny * g.nz;
     L.tab.count = h->count;
     L.tab.nblk_full = bf;
     L.tab.nblk_half = bh;
@@ -223,6 +226,9 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
     if (mixed) {
       L.o_r32 = take(sizeof(float) * L.n);
       L.o_z32 = take(sizeof(float) * L.n);
+    } else if (h->opt.block_fp) {
+      L.o_zq = take(sizeof(long long) * L.n);
+      L.o_ze = take(sizeof(int) * L.nlines);
     }
     if (h->batch == 0) {  // a diagonal field can be bound to a single-grid handle
       L.o_kap = take(sizeof(double) * L.n);
@@ -266,6 +272,9 @@ static int bind(hpcg_ctx *h, char *ws, size_t bytes, bool owned) {
     L.z = l > 0 ? (double *)(ws + L.o_z) : nullptr;
     L.r32 = h->opt.precision == HPCG_MIXED ? (float *)(ws + L.o_r32) : nullptr;
     L.z32 = h->opt.precision == HPCG_MIXED ? (float *)(ws + L.o_z32) : nullptr;
+    const bool bfp_space = h->opt.precision != HPCG_MIXED && h->opt.block_fp;
+    L.zq = bfp_space ? (long long *)(ws + L.o_zq) : nullptr;
+    L.ze = bfp_space ? (int *)(ws + L.o_ze) : nullptr;
     if (h->batch == 0) {
       L.kap = (double *)(ws + L.o_kap);
       L.invd = (double *)(ws + L.o_invd);
@@ -647,6 +656,90 @@ static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s
 }
 
 
+// ---------------------------------------------------------------------------
+// The FP64 V-cycle with z in block floating point (hpcg_bfp.cuh): the same
+// runs, restriction and refinement as enqueue_vcycle_t, on the level arrays
+// zq (mantissas) and ze (line exponents).
+template <int NC>
+static void launch_gs_bfp(const LevelData &L, int count, int py, int pz, int pa, int steps, int vmask, const double *r, const double *invd,
+                          const CgState *st, const Inst *tabc, double *rc, const double *kap, double *zout, cudaStream_t s) {
+  launch_k(k_gs_lines_bfp<NC>, dim3(L.tab.nblk_line), dim3(32, L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py,
+           pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout);
+}
+
+static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, int steps, const double *r, cudaStream_t s,
+                                  const CgState *st, int vmask, double *rc, double *zout) {
+  const LevelData &L = h->lv[l];
+  const double *invd = invd_of<double>(L, h->has_kappa);
+  const double *kap = kap_of<double>(L, h->has_kappa);
+  const Inst *tabc = rc ? h->lv[l + 1].tab.inst : nullptr;
+  switch (L.tab.nch2) {
+#define HPCG_BFP_CASE(N) \
+  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, s); break;
+    HPCG_BFP_CASE(1) HPCG_BFP_CASE(2) HPCG_BFP_CASE(3) HPCG_BFP_CASE(4) HPCG_BFP_CASE(5) HPCG_BFP_CASE(6)
+#undef HPCG_BFP_CASE
+    default: return HPCG_ERR_UNSUPPORTED;
+  }
+  CKL("k_gs_lines_bfp");
+  return HPCG_OK;
+}
+
+// One smoother application (`sweeps` symmetric sweeps) on level l, grouped
+// into runs as in enqueue_smoother.  rc (nullable): residual + injection
+// fused into the last run, which for the symmetric smoother is class (0,0)
+// ending on even x.  zout (nullable): the FP64 z, written by the last run of
+// every line class.
+static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps, cudaStream_t s, const CgState *st, bool from_zero,
+                                double *rc, double *zout) {
+  const std::vector<int> seq = phase_sequence(sweeps, 1);
+  std::vector<std::pair<int, int>> runs;  // (first colour, steps)
+  for (size_t i = 0; i < seq.size();) {
+    size_t j = i + 1;
+    while (j < seq.size() && (seq[j] >> 1) == (seq[i] >> 1)) ++j;
+    runs.push_back({seq[i], (int)(j - i)});
+    i = j;
+  }
+  int vmask = from_zero ? 0 : 0xF;
+  for (size_t i = 0; i < runs.size(); ++i) {
+    const int k = runs[i].first, steps = runs[i].second, cls = k >> 1;
+    bool last_of_class = true;
+    for (size_t j = i + 1; j < runs.size(); ++j) last_of_class = last_of_class && (runs[j].first >> 1) != cls;
+    const int last_parity = (steps & 1) ? (k & 1) : 1 - (k & 1);
+    double *rc_here = (rc && i + 1 == runs.size()) ? rc : nullptr;
+    if (steps < 2 || (rc_here && (cls != 0 || last_parity != 0))) return HPCG_ERR_UNSUPPORTED;
+    TRY(enqueue_line_steps_bfp(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, s, st, vmask, rc_here, last_of_class ? zout : nullptr));
+    prof_mark(PK_SMOOTH, l);
+    vmask |= 1 << cls;
+  }
+  return HPCG_OK;
+}
+
+static int enqueue_prolong_bfp(hpcg_ctx *h, int l, cudaStream_t s, const CgState *st) {
+  const LevelData &F = h->lv[l], &C = h->lv[l + 1];
+  launch_k(k_prolong_bfp, dim3((unsigned)((C.nlines + 7) / 8)), dim3(32, 8), 0, s, F.tab.inst, C.tab.inst, h->count, (int)C.nlines,
+           (const long long *)C.zq, (const int *)C.ze, F.zq, F.ze, st);
+  CKL("k_prolong_bfp");
+  prof_mark(PK_PROLONG, l);
+  return HPCG_OK;
+}
+
+// Listing 1 on levels 0..L-1: r is the finest right-hand side (FP64), z the
+// FP64 result on the finest level.
+static int enqueue_vcycle_bfp(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st) {
+  const int L = h->levels;
+  for (int l = 0; l < L; ++l) {
+    const bool coarsest = l == L - 1;
+    TRY(enqueue_smoother_bfp(h, l, l == 0 ? r : h->lv[l].r, coarsest ? 1 : h->opt.pre_sweeps, s, st, true,
+                             coarsest ? nullptr : h->lv[l + 1].r, (coarsest && l == 0) ? z : nullptr));
+    if (coarsest) break;
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    TRY(enqueue_prolong_bfp(h, l, s, st));                                                                  // z <- z + refine(z_c)
+    TRY(enqueue_smoother_bfp(h, l, l == 0 ? r : h->lv[l].r, h->opt.post_sweeps, s, st, false, nullptr, l == 0 ? z : nullptr));
+  }
+  return HPCG_OK;
+}
+
 // Listing 1 on levels 0..L-1; rl[l], zl[l] are the level vectors in precision T.
 template <typename T>
 static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_t s, const CgState *st) {
@@ -707,6 +800,8 @@ static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t 
     }
     return HPCG_OK;
   }
+  if (h->use_bfp && h->tail_first <= 0 && ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(z)) & 15) == 0)
+    return enqueue_vcycle_bfp(h, r, z, s, st);
   double *rl[kMaxLevels], *zl[kMaxLevels];
   rl[0] = const_cast<double *>(r);
   zl[0] = z;
@@ -952,6 +1047,8 @@ static int time_shape(hpcg_ctx *h, int l, bool rows, int lpc, int zc, cudaStream
       rc = enqueue_spmv<double, 0>(h, l, a, nullptr, b, nullptr, nullptr, nullptr, s);
     else if (h->opt.precision == HPCG_MIXED)  // the V-cycle runs the FP32 kernel
       rc = enqueue_line_steps<float>(h, l, 0, 0, 0, 2, L.r32, L.z32, s, nullptr);
+    else if (h->use_bfp)  // ... or the block-floating-point one
+      rc = enqueue_line_steps_bfp(h, l, 0, 0, 0, 2, a, s, nullptr, 0xF, nullptr, nullptr);
     else
       rc = enqueue_line_steps<double>(h, l, 0, 0, 0, 2, a, b, s, nullptr);
   }
@@ -981,6 +1078,8 @@ static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s) {
       CK(cudaMemsetAsync(L.r32, 0, sizeof(float) * L.n, s));
       CK(cudaMemsetAsync(L.z32, 0, sizeof(float) * L.n, s));
     }
+    if (h->use_bfp)  // valid (zero) lines and exponents to time on
+      TRY(enqueue_smoother_bfp(h, l, a, 1, s, nullptr, true, nullptr, nullptr));
     for (int pass = 0; pass < 2; ++pass) {
       const bool rows = pass == 0;
       float best = 1e30f;
@@ -1159,6 +1258,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->fixed_point = 1;
   opt->pdl = 1;
   opt->persistent = 0;
+  opt->block_fp = 1;
   return HPCG_OK;
 }
 
@@ -1168,6 +1268,15 @@ static int make_handle(const hpcg_options *opt, const std::vector<int> &dims, in
   h->batch = batch;
   h->levels = opt->levels;
   plan(h, dims);
+  // block floating point needs the colour-pair line kernels on every level
+  // (lines of at most 6 x 64 points), even line lengths (its kernels move
+  // x pairs as 16-byte vectors) and a smoother whose last run restricts
+  bool bfp = opt->block_fp && opt->precision == HPCG_FP64 && opt->fixed_point && opt->symmetric && !opt->persistent;
+  for (int l = 0; l < h->levels; ++l) {
+    bfp = bfp && h->lv[l].tab.nch > 0 && h->lv[l].tab.nch2 >= 1 && h->lv[l].tab.nch2 <= 6;
+    for (const Inst &g : h->lv[l].inst) bfp = bfp && (g.nx % 2) == 0;
+  }
+  h->use_bfp = bfp;
   *out = h;
   return HPCG_OK;
 }

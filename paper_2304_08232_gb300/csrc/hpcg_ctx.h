@@ -44,10 +44,13 @@ struct LevelData {
   LevelTab tab{};
   long n = 0;
   // workspace offsets (bytes)
-  size_t o_tab = 0, o_r = 0, o_z = 0, o_r32 = 0, o_z32 = 0, o_kap = 0, o_invd = 0, o_kap32 = 0, o_invd32 = 0;
+  size_t o_tab = 0, o_r = 0, o_z = 0, o_r32 = 0, o_z32 = 0, o_kap = 0, o_invd = 0, o_kap32 = 0, o_invd32 = 0, o_zq = 0, o_ze = 0;
+  long nlines = 0;  // x-lines over all instances (sum of ny * nz)
   // device pointers (valid once a workspace is bound)
   double *r = nullptr, *z = nullptr, *kap = nullptr, *invd = nullptr;
   float *r32 = nullptr, *z32 = nullptr, *kap32 = nullptr, *invd32 = nullptr;
+  long long *zq = nullptr;  // block-floating-point z: mantissas [n]
+  int *ze = nullptr;        // and one exponent per x-line [nlines]
 };
 
 struct GraphCache {
@@ -81,6 +84,7 @@ struct hpcg_ctx {
   hpcg_ctx *multi = nullptr;  // internal batch of max_rhs copies of the grid (hpcg_pcg_solve_multi)
   int multi_R = 0;
   bool tuned = false;
+  bool use_bfp = false;  // the FP64 V-cycle keeps z in block floating point (hpcg_options.block_fp)
   // persistent tail of the V-cycle (levels tail_first..levels-1 in one cooperative launch)
   int tail_first = -1;        // -1: no tail
   bool tail_ok = true;        // cleared if a cooperative launch is refused

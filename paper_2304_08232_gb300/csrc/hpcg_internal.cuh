@@ -77,7 +77,8 @@ __host__ __device__ inline int tiles_of(int nx, int ny, int nz) {
 }
 __host__ __device__ inline int half_up(int v) { return (v + 1) / 2; }
 
-// Finds the instance that owns global block `b` (prefix `which` in the table);
+// Finds the instance that owns global block `b` (prefix `which` in the table;
+// Which = 5: the instance owning global x-line `b` of a level);
 // tables hold at most a few hundred entries, a binary search is uniform per block.
 template <int Which>
 __device__ inline int find_inst(const Inst *__restrict__ tab, int count, int b) {
@@ -88,7 +89,8 @@ __device__ inline int find_inst(const Inst *__restrict__ tab, int count, int b) 
                 : Which == 1 ? tab[mid].blk_half
                 : Which == 2 ? tab[mid].blk_red
                 : Which == 3 ? tab[mid].blk_row
-                             : tab[mid].blk_line;
+                : Which == 4 ? tab[mid].blk_line
+                             : tab[mid].poff;
     if (start <= b) lo = mid; else hi = mid - 1;
   }
   return lo;
