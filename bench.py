@@ -335,12 +335,38 @@ def run_gpu(args):
                               "shapes": json.loads(args.shapes) if args.shapes else "autotuned"}), flush=True)
         return 0
 
-    # --- dominant kernel: the colour-pair line kernel (k_gs_lines<double>) on
-    # the finest level, timed over whole smoother applications (7 launches:
-    # runs [0,1] [2,3] [4,5] [6,7,6] [5,4] [3,2] [1,0]) with CUDA events on
-    # the launching stream (torch's current stream)
+    # --- dominant kernel: the block-floating-point colour-pair kernel
+    # k_gs_lines_bfp on the finest level, as the FP64 solve runs it: every
+    # launch of one CG iteration is bracketed by CUDA events on the launching
+    # stream (hpcg_profile_iteration), 14 launches on the finest level (pre-
+    # and post-smoother, 7 runs each: [0,1] [2,3] [4,5] [6,7,6] [5,4] [3,2]
+    # [1,0]); the median of 5 iterations.
     shapes = tuned_shapes(prob)
-    zc = shapes[0][3]
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+    l0_ms = sorted(prob.profile_iteration(b)["smoother_ms"][0] for _ in range(5))[2]
+    launches_l0 = 7 * 2
+    k_ms = l0_ms / launches_l0
+    # Per launch it must read z of every line (the off-line neighbours of a
+    # class are the other three classes, plus its own line: 8 n bytes of int64
+    # mantissas), r of its class lines (2 n) and write its class lines (2 n):
+    # 12 n bytes.  It issues no FP64 instruction without kappa (the division by
+    # 26 is an integer multiply-high), so HBM bounds it: 12 n / HBM = 12.5 us
+    # at 192^3.
+    bytes_launch = 12 * n
+    achieved_gbs = bytes_launch / (k_ms * 1e-3) / 1e9
+    # DRAM traffic of one finest-level launch (post-smoother run [0,1]) from an
+    # ncu capture at 192^3 (profiles/k_gs_lines_bfp_192cubed.md)
+    traffic = (71.032064e6 + 0.534016e6) if (NX, NY, NZ) == (192, 192, 192) else None
+    roofline = {"bound": "hbm", "kernel": "k_gs_lines_bfp<3> (finest level, colour-pair runs of the V-cycle)",
+                "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
+                "bytes_algorithmic_per_launch": bytes_launch, "traffic": traffic,
+                "ms_per_launch": k_ms, "launches_timed": launches_l0,
+                "timing": "CUDA events around every launch of one CG iteration (hpcg_profile_iteration), median of 5",
+                "launch_shapes_per_level": shapes}
+    # The FP64-storage colour kernel (k_gs_lines_fx: hpcg_rbgs, and the V-cycle
+    # with block_fp = 0) for comparison: one symmetric sweep, 7 launches
     r = torch.randn(n, dtype=torch.float64, device=dev)
     z = torch.randn(n, dtype=torch.float64, device=dev)
     for _ in range(3):
@@ -355,36 +381,10 @@ def run_gpu(args):
     k1.record(stream)
     torch.cuda.synchronize()
     sweep_ms = k0.elapsed_time(k1) / reps
-    launches_per_sweep = 7
-    k_ms = sweep_ms / launches_per_sweep
-    # Roofline of the colour-pair kernel k_gs_lines_fx.  Per launch it must read
-    # z of every line (8 n bytes: the off-line neighbours of a class are the
-    # other three classes, plus its own line), r of its class lines (2 n) and
-    # write z of its class lines (2 n): 12 n bytes.  Its FP64 work is the colour
-    # update, 4 instructions (3 additions, 1 multiply by 1/A_ii) per updated
-    # row; the 24 off-line neighbour sums run exactly in fixed point on the
-    # integer pipe.  Speed of light at 192^3: 12 n / HBM = 12.5 us against
-    # 30 n/4 FP64 instructions / 629 G/s = 8.4 us, so HBM bounds it.
-    peaks, peak_kind = measured_peaks()
-    hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
-    ops_sweep = (n // 4) * (6 * 4 + 4 * 1.5)  # six two-step runs, one three-step run [6,7,6]
-    fp64_rate = ops_sweep / (sweep_ms * 1e-3) / 1e9
-    peak_nominal = 152 * 2 * 2070e6 / 1e9  # FP64 instructions per second (2 per SM per clock)
-    bytes_launch = 12 * n
-    achieved_gbs = bytes_launch / (k_ms * 1e-3) / 1e9
-    # DRAM traffic of one launch from the ncu capture of the same kernel on a
-    # 192 x 192 x 512 grid (profiles/k_gs_lines_fx_192x192x512.md), scaled to
-    # 192^3 by the row count (traffic per row is constant)
-    traffic = (189.598464e6 + 21.898240e6) * n / (192 * 192 * 512) if (NX, NY, NZ) == (192, 192, 192) else None
-    roofline = {"bound": "hbm", "kernel": "k_gs_lines_fx<3> (finest level, colour-pair runs of a symmetric sweep)",
-                "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-                "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
-                "bytes_algorithmic_per_launch": bytes_launch, "traffic": traffic,
-                "ms_per_launch": k_ms, "ms_per_sweep": sweep_ms, "launches_per_sweep": launches_per_sweep,
-                "fp64": {"instr_per_sweep": ops_sweep, "g_instr_s": fp64_rate, "peak_g_instr_s": peak_nominal,
-                         "frac": fp64_rate / peak_nominal,
-                         "peak_basis": "152 SMs x 2 FP64 instructions/clk x 2070 MHz"},
-                "launch_shapes_per_level": shapes}
+    roofline["fp64_storage_kernel"] = {"kernel": "k_gs_lines_fx<3>", "ms_per_launch": sweep_ms / 7,
+                                       "achieved_gbs": bytes_launch / (sweep_ms / 7 * 1e-3) / 1e9,
+                                       "fp64_instr_per_updated_row": 4}
+    del r, z
     # SpMV line kernel (secondary): 7 + 4/zc FP64 instructions per row
     zr = shapes[0][1]
     xs_ = torch.randn(n, dtype=torch.float64, device=dev)
@@ -426,8 +426,8 @@ def run_gpu(args):
                      "x": xs}
     # the same FP64 solve in other configurations of the library
     variants = {}
-    for name, kw in [("persistent_coarse_kernel", {"persistent": True}), ("plain_fp64_sums", {"fixed_point": False}),
-                     ("no_programmatic_dependent_launch", {"pdl": False})]:
+    for name, kw in [("fp64_storage_in_vcycle", {"block_fp": False}), ("persistent_coarse_kernel", {"persistent": True}),
+                     ("plain_fp64_sums", {"fixed_point": False}), ("no_programmatic_dependent_launch", {"pdl": False})]:
         p_v = HpcgProblem(NX, NY, NZ, levels=LEVELS, device=dev, **kw)
         xv = torch.zeros(n, dtype=torch.float64, device=dev)
         p_v.pcg_solve(b, max_iters=ITERS, tol=0.0, out=xv)
