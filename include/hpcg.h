@@ -85,6 +85,11 @@ typedef struct {
                        values of the line's typical size, an absolute 2^-56 of its largest), and
                        non-finite values end as NaN; r and the result z stay FP64.  0: the FP64
                        V-cycle keeps z in FP64 */
+  int cluster_tail; /* 1: with block_fp, the levels of at most 32768 rows whose x-lines fit 64
+                       points run in one launch of a 16-block thread-block cluster, runs separated
+                       by the cluster barrier instead of kernel boundaries (same bits as one launch
+                       per run); 0 (default): one launch per run on every level, which measured
+                       faster on one 192^3 grid (16 SMs do the coarse runs slower than launches) */
 } hpcg_options;
 
 typedef struct {

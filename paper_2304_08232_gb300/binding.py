@@ -59,7 +59,7 @@ class HpcgProblem:
 
     def __init__(self, nx, ny, nz, levels=4, precision="fp64", kappa=None, pre_sweeps=1, post_sweeps=1,
                  symmetric=True, max_rhs=0, check_every=1, persistent=False, fixed_point=True, pdl=True, block_fp=True,
-                 device=None):
+                 cluster_tail=False, device=None):
         self.lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("HpcgProblem needs a CUDA device")
@@ -76,6 +76,7 @@ class HpcgProblem:
         opt.fixed_point = 1 if fixed_point else 0
         opt.pdl = 1 if pdl else 0
         opt.block_fp = 1 if block_fp else 0
+        opt.cluster_tail = 1 if cluster_tail else 0
         self.dims = (nx, ny, nz)
         self.levels = levels
         self.precision = precision

@@ -27,6 +27,7 @@
 // line class (the final-touch runs of the last post-smoother).
 #pragma once
 #include "hpcg_fixed.cuh"
+#include "hpcg_tail.cuh"
 
 namespace hpcg {
 
@@ -43,14 +44,14 @@ __device__ __forceinline__ double bfp_nan() { return __longlong_as_double(0x7ff8
 
 // Mantissa pairs (x = 2k, 2k+1 for k = lane + 32c) of one line; nx is even,
 // so a pair is either inside the line or past its end.
-template <int NC>
+template <int NC, bool COH = false>
 __device__ __forceinline__ void ld_pairs_q(const long long *__restrict__ line, bool ok, int nx, int lane, long long (&e)[NC],
                                            long long (&o)[NC]) {
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const int xe = 64 * c + 2 * lane;
     if (ok && xe < nx) {
-      const longlong2 v = __ldg(reinterpret_cast<const longlong2 *>(line + xe));
+      const longlong2 v = ld_line<COH>(reinterpret_cast<const longlong2 *>(line + xe));
       e[c] = v.x;
       o[c] = v.y;
     } else {
@@ -59,13 +60,13 @@ __device__ __forceinline__ void ld_pairs_q(const long long *__restrict__ line, b
     }
   }
 }
-template <int NC>
+template <int NC, bool COH = false>
 __device__ __forceinline__ void ld_pairs_d(const double *__restrict__ line, int nx, int lane, double (&e)[NC], double (&o)[NC]) {
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const int xe = 64 * c + 2 * lane;
     if (xe < nx) {
-      const double2 v = __ldg(reinterpret_cast<const double2 *>(line + xe));
+      const double2 v = ld_line<COH>(reinterpret_cast<const double2 *>(line + xe));
       e[c] = v.x;
       o[c] = v.y;
     } else {
@@ -77,19 +78,19 @@ __device__ __forceinline__ void ld_pairs_d(const double *__restrict__ line, int 
 
 // Sum over lines y-1, y, y+1 of plane zz (those with ok set), at the largest
 // exponent of the three; returns that exponent.
-template <int NC>
+template <int NC, bool COH = false>
 __device__ __forceinline__ int bfp_plane_sum(const long long *__restrict__ qg, const int *__restrict__ eg, int nx, int ny, long sxy, int y,
                                              int zz, bool oka, bool okb, bool okd, int lane, long long (&te)[NC], long long (&to)[NC]) {
   const long li = (long)zz * ny + y;
-  const int ea = oka ? __ldg(eg + li - 1) : kFxMinE;
-  const int eb = okb ? __ldg(eg + li) : kFxMinE;
-  const int ed = okd ? __ldg(eg + li + 1) : kFxMinE;
+  const int ea = oka ? ld_line<COH>(eg + li - 1) : kFxMinE;
+  const int eb = okb ? ld_line<COH>(eg + li) : kFxMinE;
+  const int ed = okd ? ld_line<COH>(eg + li + 1) : kFxMinE;
   const int et = max(max(ea, eb), ed);
   const long long *la = qg + (long)zz * sxy + (long)(y - 1) * nx;
   long long ae[NC], ao[NC], be[NC], bo[NC], de[NC], d_o[NC];
-  ld_pairs_q<NC>(la, oka, nx, lane, ae, ao);
-  ld_pairs_q<NC>(la + nx, okb, nx, lane, be, bo);
-  ld_pairs_q<NC>(la + 2 * nx, okd, nx, lane, de, d_o);
+  ld_pairs_q<NC, COH>(la, oka, nx, lane, ae, ao);
+  ld_pairs_q<NC, COH>(la + nx, okb, nx, lane, be, bo);
+  ld_pairs_q<NC, COH>(la + 2 * nx, okd, nx, lane, de, d_o);
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     te[c] = (shr_q(ae[c], et - ea) + shr_q(be[c], et - eb)) + shr_q(de[c], et - ed);
@@ -116,21 +117,23 @@ __device__ __forceinline__ long long bfp_new_value(long long t, int S, int sout,
 // holding valid z (others read as zero).  rc (nullable): fused residual +
 // injection into the FP64 right-hand side of level l+1 (runs of class (0,0)
 // ending on even x).  zout (nullable): FP64 copy of the updated lines.
-template <int NC>
-__global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
-                                                      int steps, int vmask, const double *__restrict__ r, long long *__restrict__ zq,
-                                                      int *__restrict__ ze, const double *__restrict__ invd, const CgState *__restrict__ st,
-                                                      const Inst *__restrict__ tabc, double *__restrict__ rc,
-                                                      const double *__restrict__ kap, double *__restrict__ zout) {
-  pdl_enter();
-  const int blk = blockIdx.x;
-  const int ii = find_inst<4>(tab, count, blk);
-  const Inst g = tab[ii];
-  if (st && st[ii].done) return;
+// The work of block `blk` (warp wy of it) of a launch of k_gs_lines_bfp; COH:
+// load with L2-coherent loads (data written earlier in the same launch).
+// g1: the grid when count == 1 (a kernel parameter, so that a single grid's
+// launch does not wait for a table load before its first data loads).
+template <int NC, bool COH>
+__device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__restrict__ tab, const Inst &g1, int count, int lpc, int zc,
+                                             int py, int pz, int pa, int steps, int vmask, const double *__restrict__ r,
+                                             long long *__restrict__ zq, int *__restrict__ ze, const double *__restrict__ invd,
+                                             const CgState *__restrict__ st, const Inst *__restrict__ tabc, double *__restrict__ rc,
+                                             const double *__restrict__ kap, double *__restrict__ zout) {
+  const int ii = count == 1 ? 0 : find_inst<4>(tab, count, blk);
+  const Inst g = count == 1 ? g1 : tab[ii];
+  const int done = st ? ld_line<COH>(&st[ii].done) : 0;  // tested once the first loads are issued
   const int cy = (g.ny - py + 1) / 2, cz = (g.nz - pz + 1) / 2;
   const int nby = (half_up(g.ny) + lpc - 1) / lpc;
   const int lb = blk - g.blk_line;
-  const int j = (lb % nby) * lpc + threadIdx.y;
+  const int j = (lb % nby) * lpc + wy;
   const int m0 = (lb / nby) * zc;
   const int m1 = min(m0 + zc, cz);
   if (j >= cy || m0 >= m1) return;  // whole warp
@@ -152,25 +155,37 @@ __global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ t
   {
     const int zz = 2 * m0 + pz - 1;
     const bool zin = zz >= 0;
-    Ec = bfp_plane_sum<NC>(qg, eg, nx, ny, sxy, y, zz, zin && y - 1 >= 0 && vyo, zin && vy0, zin && y + 1 < ny && vyo, lane, tpe, tpo);
+    Ec = bfp_plane_sum<NC, COH>(qg, eg, nx, ny, sxy, y, zz, zin && y - 1 >= 0 && vyo, zin && vy0, zin && y + 1 < ny && vyo, lane, tpe,
+                                tpo);
   }
+  if (done) return;  // converged instance: nothing changes
   for (int m = m0; m < m1; ++m) {
     const int zz = 2 * m + pz;
     const bool zin = zz + 1 < nz;
     long long te[NC], to[NC];
-    const int et = bfp_plane_sum<NC>(qg, eg, nx, ny, sxy, y, zz + 1, zin && y - 1 >= 0 && vyo, zin && vy0, zin && y + 1 < ny && vyo, lane,
-                                     te, to);
+    const int et = bfp_plane_sum<NC, COH>(qg, eg, nx, ny, sxy, y, zz + 1, zin && y - 1 >= 0 && vyo, zin && vy0, zin && y + 1 < ny && vyo,
+                                          lane, te, to);
     const long li = (long)zz * ny + y;
     const long rowbase = (long)zz * sxy + (long)y * nx;
-    const int eu = ym ? __ldg(eg + li - 1) : kFxMinE;
-    const int ew = yp ? __ldg(eg + li + 1) : kFxMinE;
-    const int eo = own_valid ? eg[li] : kFxMinE;
+    const int eu = ym ? ld_line<COH>(eg + li - 1) : kFxMinE;
+    const int ew = yp ? ld_line<COH>(eg + li + 1) : kFxMinE;
+    const int eo = own_valid ? (COH ? __ldcg(eg + li) : eg[li]) : kFxMinE;
     long long ue[NC], uo[NC], we[NC], wo[NC], qe[NC], qo[NC];
-    ld_pairs_q<NC>(qg + rowbase - nx, ym, nx, lane, ue, uo);
-    ld_pairs_q<NC>(qg + rowbase + nx, yp, nx, lane, we, wo);
-    ld_pairs_q<NC>(qg + rowbase, own_valid, nx, lane, qe, qo);
+    ld_pairs_q<NC, COH>(qg + rowbase - nx, ym, nx, lane, ue, uo);
+    ld_pairs_q<NC, COH>(qg + rowbase + nx, yp, nx, lane, we, wo);
+    if (own_valid && COH) {
+      ld_pairs_q<NC, true>(qg + rowbase, true, nx, lane, qe, qo);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {  // own line: written only by this warp
+        const int xe = 64 * c + 2 * lane;
+        const longlong2 v = (own_valid && xe < nx) ? *reinterpret_cast<const longlong2 *>(qg + rowbase + xe) : make_longlong2(0, 0);
+        qe[c] = v.x;
+        qo[c] = v.y;
+      }
+    }
     double rE[NC], rO[NC];
-    ld_pairs_d<NC>(rg + rowbase, nx, lane, rE, rO);
+    ld_pairs_d<NC, COH>(rg + rowbase, nx, lane, rE, rO);
     // off-line sums: column sums at x (both planes beside + the two lines beside), then over x-1..x+1
     const int E = max(max(Ec, et), max(eu, ew));
     long long PE[NC], PO[NC];
@@ -313,16 +328,25 @@ __global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ t
   }
 }
 
-// Refinement z_f <- z_f + R^T z_c on the block-floating-point vectors: one
-// warp per coarse line (yc, zc), which feeds the even points of fine line
-// (2 yc, 2 zc).  The fine line moves to exponent max(e_f, e_c) + 1, which
-// keeps the sums below 2^58.
-__global__ void __launch_bounds__(256) k_prolong_bfp(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count, int nlines,
-                                                     const long long *__restrict__ qc, const int *__restrict__ ec,
-                                                     long long *__restrict__ qf, int *__restrict__ ef, const CgState *__restrict__ st) {
+template <int NC>
+__global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
+                                                      int steps, int vmask, const double *__restrict__ r, long long *__restrict__ zq,
+                                                      int *__restrict__ ze, const double *__restrict__ invd, const CgState *__restrict__ st,
+                                                      const Inst *__restrict__ tabc, double *__restrict__ rc,
+                                                      const double *__restrict__ kap, double *__restrict__ zout, const Inst g1) {
   pdl_enter();
-  const int wl = blockIdx.x * (blockDim.y) + threadIdx.y;
-  if (wl >= nlines) return;
+  gs_bfp_block<NC, false>(blockIdx.x, threadIdx.y, tab, g1, count, lpc, zc, py, pz, pa, steps, vmask, r, zq, ze, invd, st, tabc, rc, kap,
+                          zout);
+}
+
+// Refinement z_f <- z_f + R^T z_c on the block-floating-point vectors for
+// coarse line wl (all instances' lines numbered in order), which feeds the
+// even points of fine line (2 yc, 2 zc).  The fine line moves to exponent
+// max(e_f, e_c) + 1, which keeps the sums below 2^58.
+template <bool COH>
+__device__ __forceinline__ void prolong_bfp_line(int wl, int lane, const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count,
+                                                 const long long *__restrict__ qc, const int *__restrict__ ec, long long *__restrict__ qf,
+                                                 int *__restrict__ ef, const CgState *__restrict__ st) {
   const int ii = find_inst<5>(tabc, count, wl);
   if (st && st[ii].done) return;
   const Inst gc = tabc[ii], gf = tabf[ii];
@@ -330,18 +354,108 @@ __global__ void __launch_bounds__(256) k_prolong_bfp(const Inst *__restrict__ ta
   const int yc = li % gc.ny, zc = li / gc.ny;
   const int yf = 2 * yc, zf = 2 * zc;
   const long lf = (long)zf * gf.ny + yf;
-  const int e_f = ef[gf.poff + lf], e_c = __ldg(ec + gc.poff + li);
+  const int e_f = COH ? __ldcg(ef + gf.poff + lf) : ef[gf.poff + lf];
+  const int e_c = ld_line<COH>(ec + gc.poff + li);
   const bool bad = e_f > kFxMaxE || e_c > kFxMaxE;
   const int S = max(e_f, e_c) + 1;
   long long *fl = qf + gf.off + lf * gf.nx;
   const long long *cl = qc + gc.off + (long)li * gc.nx;
-  for (int xe = 2 * threadIdx.x; xe < gf.nx; xe += 64) {
-    const longlong2 v = *reinterpret_cast<const longlong2 *>(fl + xe);
-    const long long c = __ldg(cl + (xe >> 1));
+  for (int xe = 2 * lane; xe < gf.nx; xe += 64) {
+    const longlong2 v = COH ? __ldcg(reinterpret_cast<const longlong2 *>(fl + xe)) : *reinterpret_cast<const longlong2 *>(fl + xe);
+    const long long c = ld_line<COH>(cl + (xe >> 1));
     *reinterpret_cast<longlong2 *>(fl + xe) =
         bad ? make_longlong2(0, 0) : make_longlong2(shr_q(v.x, S - e_f) + shr_q(c, S - e_c), shr_q(v.y, S - e_f));
   }
-  if (threadIdx.x == 0) ef[gf.poff + lf] = bad ? kBfpNaN : S;
+  if (lane == 0) ef[gf.poff + lf] = bad ? kBfpNaN : S;
+}
+
+// One launch: one warp per coarse line of every instance.
+__global__ void __launch_bounds__(256) k_prolong_bfp(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count, int nlines,
+                                                     const long long *__restrict__ qc, const int *__restrict__ ec,
+                                                     long long *__restrict__ qf, int *__restrict__ ef, const CgState *__restrict__ st) {
+  pdl_enter();
+  const int wl = blockIdx.x * blockDim.y + threadIdx.y;
+  if (wl < nlines) prolong_bfp_line<false>(wl, threadIdx.x, tabf, tabc, count, qc, ec, qf, ef, st);
+}
+
+// ---------------------------------------------------------------------------
+// The coarse end of the V-cycle in one launch of one thread-block cluster.
+//
+// On the smallest levels every run is a few microseconds of work, and one
+// launch per run costs more than the work.  Here the levels first..last (at
+// most kBfpTailRows rows each, one 64-point chunk per line) run their
+// pre-smoothers (restriction fused into each level's last run), the coarsest
+// level's smoother, then refinement and post-smoothers back up to `first`,
+// inside one kernel whose kBfpTailCtas blocks form one cluster.  Runs are
+// separated by the cluster's hardware barrier (release/acquire at cluster
+// scope); data written earlier in the launch is read with L2-coherent loads.
+// Every block executes the same barrier sequence, so the barrier always
+// completes.  The arithmetic is that of k_gs_lines_bfp / k_prolong_bfp, so
+// the results are the same bits as one launch per run.
+constexpr int kBfpTailCtas = 16;
+constexpr int kBfpTailWarps = 16;  // warps per block of the cluster kernel
+constexpr long kBfpTailRows = 32768;
+
+struct BfpTailLevel {
+  const Inst *tab;
+  Inst g1;                        // tab[0] (used when the handle has one grid)
+  const double *r;                // right-hand side of the level (FP64)
+  long long *zq;                  // block-floating-point z
+  int *ze;
+  const double *invd, *kap;       // kappa fields, or null
+  double *rnext;                  // right-hand side of level + 1 (fused restriction), null on the coarsest
+  const Inst *tabnext;
+  int lpc, zc, nblk_line, nlines;  // colour-line launch shape and its blocks; x-lines of the level
+  int npre, npost;
+  TailRun pre[kTailRuns], post[kTailRuns];
+};
+
+struct BfpTailPlan {
+  int first, last, count, pad;
+  BfpTailLevel lv[kMaxLevels];
+};
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int NC>
+__device__ __forceinline__ void bfp_tail_runs(const BfpTailPlan &P, int l, const TailRun *runs, int nruns, bool from_zero, bool fuse,
+                                              const CgState *st) {
+  const BfpTailLevel &L = P.lv[l];
+  int vmask = from_zero ? 0 : 0xF;
+  const int vpb = kBfpTailWarps / L.lpc;  // virtual blocks per block step
+  const int w = threadIdx.y;
+  for (int k = 0; k < nruns; ++k) {
+    const TailRun run = runs[k];
+    double *rc = (fuse && k == nruns - 1) ? L.rnext : nullptr;
+    if (w < vpb * L.lpc) {
+      for (int base = blockIdx.x * vpb; base < L.nblk_line; base += gridDim.x * vpb) {
+        const int vb = base + w / L.lpc;
+        if (vb < L.nblk_line)
+          gs_bfp_block<NC, true>(vb, w % L.lpc, L.tab, L.g1, P.count, L.lpc, L.zc, run.cls & 1, (run.cls >> 1) & 1, run.pa, run.steps,
+                                 vmask, L.r, L.zq, L.ze, L.invd, st, rc ? L.tabnext : nullptr, rc, L.kap, nullptr);
+      }
+    }
+    vmask |= 1 << run.cls;
+    cluster_barrier();
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(32 * kBfpTailWarps) k_vcycle_tail_bfp(const BfpTailPlan *__restrict__ plan,
+                                                                         const CgState *__restrict__ st) {
+  pdl_enter();
+  const BfpTailPlan &P = *plan;
+  for (int l = P.first; l <= P.last; ++l) bfp_tail_runs<NC>(P, l, P.lv[l].pre, P.lv[l].npre, true, l < P.last, st);
+  for (int l = P.last - 1; l >= P.first; --l) {
+    const BfpTailLevel &F = P.lv[l], &C = P.lv[l + 1];
+    const int nw = gridDim.x * blockDim.y;
+    for (int wl = blockIdx.x * blockDim.y + threadIdx.y; wl < C.nlines; wl += nw)
+      prolong_bfp_line<true>(wl, threadIdx.x, F.tab, C.tab, P.count, C.zq, C.ze, F.zq, F.ze, st);
+    cluster_barrier();
+    bfp_tail_runs<NC>(P, l, F.post, F.npost, false, false, st);
+  }
 }
 
 }  // namespace hpcg

@@ -213,6 +213,7 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
   h->o_part = take(sizeof(double) * h->npart);
   h->o_out = take(sizeof(double) * (h->count + 64));
   h->o_tail = take(2 * sizeof(TailPlan));
+  h->o_tail_bfp = take(sizeof(BfpTailPlan));
   h->o_sync = take(64);
   const long n0 = L0.n;
   h->o_cg = take(sizeof(double) * 4 * (size_t)n0);
@@ -386,7 +387,81 @@ static int make_runs(int sweeps, int symmetric, TailRun *out, int cap) {
 
 // Chooses the levels of the persistent tail (small levels whose lines fit one
 // 32-wide chunk per parity) and writes the FP64 and FP32 tail plans.
+static int build_bfp_tail(hpcg_ctx *h);
+static int build_fp64_tail(hpcg_ctx *h);
 static int build_tail_plans(hpcg_ctx *h) {
+  TRY(build_fp64_tail(h));
+  return build_bfp_tail(h);
+}
+
+// The block-floating-point coarse end (k_vcycle_tail_bfp): the levels from
+// `first` down with at most kBfpTailRows rows and one 64-point chunk per x
+// parity, if this GPU can run a cluster of kBfpTailCtas blocks.
+static int build_bfp_tail(hpcg_ctx *h) {
+  h->bfp_tail_first = -1;
+  if (!h->use_bfp || !h->opt.cluster_tail || h->levels < 2) return HPCG_OK;
+  int first = h->levels;
+  for (int l = h->levels - 1; l >= 1; --l) {
+    const LevelData &L = h->lv[l];
+    if (L.tab.nch2 != 1 || L.n > kBfpTailRows) break;
+    first = l;
+  }
+  if (first >= h->levels) return HPCG_OK;
+  if (h->bfp_tail_ok < 0) {
+    int nclusters = 0;
+    cudaError_t e = cudaFuncSetAttribute(k_vcycle_tail_bfp<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kBfpTailCtas);
+      cfg.blockDim = dim3(32, kBfpTailWarps);
+      cudaLaunchAttribute a[1];
+      a[0].id = cudaLaunchAttributeClusterDimension;
+      a[0].val.clusterDim.x = kBfpTailCtas;
+      a[0].val.clusterDim.y = 1;
+      a[0].val.clusterDim.z = 1;
+      cfg.attrs = a;
+      cfg.numAttrs = 1;
+      e = cudaOccupancyMaxActiveClusters(&nclusters, k_vcycle_tail_bfp<1>, &cfg);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      nclusters = 0;
+    }
+    h->bfp_tail_ok = nclusters > 0 ? 1 : 0;
+  }
+  if (!h->bfp_tail_ok) return HPCG_OK;
+  BfpTailPlan P;
+  memset(&P, 0, sizeof(P));
+  P.first = first;
+  P.last = h->levels - 1;
+  P.count = h->count;
+  for (int l = first; l < h->levels; ++l) {
+    const LevelData &L = h->lv[l];
+    BfpTailLevel &T = P.lv[l];
+    const bool coarsest = l == h->levels - 1;
+    T.tab = L.tab.inst;
+    T.g1 = L.inst[0];
+    T.r = L.r;
+    T.zq = L.zq;
+    T.ze = L.ze;
+    T.invd = h->has_kappa ? L.invd : nullptr;
+    T.kap = h->has_kappa ? L.kap : nullptr;
+    T.rnext = coarsest ? nullptr : h->lv[l + 1].r;
+    T.tabnext = coarsest ? nullptr : h->lv[l + 1].tab.inst;
+    T.lpc = L.tab.line_lpc;
+    T.zc = L.tab.line_zc;
+    T.nblk_line = L.tab.nblk_line;
+    T.nlines = (int)L.nlines;
+    T.npre = make_runs(coarsest ? 1 : h->opt.pre_sweeps, 1, T.pre, kTailRuns);
+    T.npost = coarsest ? 0 : make_runs(h->opt.post_sweeps, 1, T.post, kTailRuns);
+    if (T.npre < 0 || T.npost < 0) return HPCG_OK;  // too many runs: no tail
+  }
+  CK(cudaMemcpy(h->ws + h->o_tail_bfp, &P, sizeof(P), cudaMemcpyHostToDevice));
+  h->bfp_tail_first = first;
+  return HPCG_OK;
+}
+
+static int build_fp64_tail(hpcg_ctx *h) {
   h->tail_first = -1;
   if (!h->tail_ok || !h->opt.persistent || h->levels < 2) return HPCG_OK;
   int first = h->levels;
@@ -664,7 +739,7 @@ template <int NC>
 static void launch_gs_bfp(const LevelData &L, int count, int py, int pz, int pa, int steps, int vmask, const double *r, const double *invd,
                           const CgState *st, const Inst *tabc, double *rc, const double *kap, double *zout, cudaStream_t s) {
   launch_k(k_gs_lines_bfp<NC>, dim3(L.tab.nblk_line), dim3(32, L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py,
-           pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout);
+           pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, L.inst[0]);
 }
 
 static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, int steps, const double *r, cudaStream_t s,
@@ -723,17 +798,39 @@ static int enqueue_prolong_bfp(hpcg_ctx *h, int l, cudaStream_t s, const CgState
   return HPCG_OK;
 }
 
+// Levels bfp_tail_first..L-1 of the V-cycle in one cluster launch.
+static int enqueue_tail_bfp(hpcg_ctx *h, cudaStream_t s, const CgState *st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kBfpTailCtas);
+  cfg.blockDim = dim3(32, kBfpTailWarps);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kBfpTailCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_vcycle_tail_bfp<1>, (const BfpTailPlan *)(h->ws + h->o_tail_bfp), st);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (e != cudaSuccess) return cuda_fail(e, "k_vcycle_tail_bfp (cluster launch)");
+  prof_mark(PK_TAIL, h->bfp_tail_first);
+  return HPCG_OK;
+}
+
 // Listing 1 on levels 0..L-1: r is the finest right-hand side (FP64), z the
 // FP64 result on the finest level.
 static int enqueue_vcycle_bfp(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st) {
   const int L = h->levels;
-  for (int l = 0; l < L; ++l) {
+  const int first = h->bfp_tail_first > 0 ? h->bfp_tail_first : L;  // levels from `first` run in the cluster kernel
+  for (int l = 0; l < first; ++l) {
     const bool coarsest = l == L - 1;
     TRY(enqueue_smoother_bfp(h, l, l == 0 ? r : h->lv[l].r, coarsest ? 1 : h->opt.pre_sweeps, s, st, true,
                              coarsest ? nullptr : h->lv[l + 1].r, (coarsest && l == 0) ? z : nullptr));
     if (coarsest) break;
   }
-  for (int l = L - 2; l >= 0; --l) {
+  if (first < L) TRY(enqueue_tail_bfp(h, s, st));
+  for (int l = (first < L ? first : L - 1) - 1; l >= 0; --l) {
     TRY(enqueue_prolong_bfp(h, l, s, st));                                                                  // z <- z + refine(z_c)
     TRY(enqueue_smoother_bfp(h, l, l == 0 ? r : h->lv[l].r, h->opt.post_sweeps, s, st, false, nullptr, l == 0 ? z : nullptr));
   }
@@ -1259,6 +1356,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->pdl = 1;
   opt->persistent = 0;
   opt->block_fp = 1;
+  opt->cluster_tail = 0;
   return HPCG_OK;
 }
 

@@ -91,6 +91,10 @@ struct hpcg_ctx {
   int tail_grid = 0;
   long long wait_limit = 2000000000LL;  // clock cycles a grid barrier may wait (about 1 s)
   size_t o_tail = 0, o_sync = 0;        // TailPlan[2] (FP64, FP32) and {barrier count, generation, error}
+  // cluster kernel of the block-floating-point V-cycle's coarse end (levels bfp_tail_first..levels-1)
+  int bfp_tail_first = -1;  // -1: none
+  int bfp_tail_ok = -1;     // -1: not checked yet; 0: the GPU cannot run the cluster
+  size_t o_tail_bfp = 0;    // BfpTailPlan
   int device = 0;
   std::mutex mu;
 };

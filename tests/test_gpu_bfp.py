@@ -92,3 +92,37 @@ def test_unaligned_vectors_take_the_fp64_path():
     rb[1:] = dev(r)
     gb.mg_vcycle(rb[1:], out=zb[1:])  # 8-byte offsets
     assert normwise(host(zb[1:]), o.mg(r)) <= TOL64
+
+
+@pytest.mark.parametrize("dims", [(64, 48, 32), (96, 96, 96), (32, 32, 64)])
+def test_cluster_tail_is_bit_identical(dims):
+    """The coarse levels in one cluster launch compute the same bits as one
+    launch per run (hpcg_options.cluster_tail)."""
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    n = int(np.prod(dims))
+    gt = HpcgProblem(*dims, levels=4, cluster_tail=True)
+    gs = HpcgProblem(*dims, levels=4, cluster_tail=False)
+    gs.set_launch_shapes(gt.autotune())
+    r = dev(normal(n, 38))
+    np.testing.assert_array_equal(host(gt.mg_vcycle(r)), host(gs.mg_vcycle(r)))
+    b = gt.get_rhs()
+    xt, st = gt.pcg_solve(b, max_iters=12, tol=0.0)
+    xs, ss = gs.pcg_solve(b, max_iters=12, tol=0.0)
+    np.testing.assert_array_equal(np.asarray(st.history), np.asarray(ss.history))
+    np.testing.assert_array_equal(host(xt), host(xs))
+    # and the profile shows the cluster kernel in place of the coarse runs
+    pr = gt.profile_iteration(b)
+    assert pr["persistent_coarse_ms"] > 0 and pr["smoother_ms"][3] == 0
+
+
+def test_cluster_tail_with_kappa_matches_oracle():
+    dims = (48, 32, 64)
+    n = int(np.prod(dims))
+    kappa = uniform(n, 0.0, 1.0, 39)
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    g = HpcgProblem(*dims, levels=4, kappa=dev(kappa), cluster_tail=True)
+    o = OracleProblem(*dims, levels=4, kappa=kappa)
+    r = normal(n, 40)
+    assert normwise(host(g.mg_vcycle(dev(r))), o.mg(r)) <= TOL64

@@ -80,8 +80,8 @@ def test_persistent_coarse_kernel_is_bit_identical(dims, precision):
     from hpcg_inputs import normal
     from paper_2304_08232_gb300 import HpcgProblem, _lib
     lib = _lib.load()
-    gp = HpcgProblem(*dims, levels=4, precision=precision, persistent=True)
-    # the persistent kernel keeps z in FP64, so compare with that form
+    # the persistent kernel keeps z in FP64: compare the two in that form
+    gp = HpcgProblem(*dims, levels=4, precision=precision, persistent=True, block_fp=False)
     gs = HpcgProblem(*dims, levels=4, precision=precision, persistent=False, block_fp=False)
     first = ctypes.c_int()
     lib.hpcg_persistent_levels(gp.h, ctypes.byref(first))
