@@ -116,7 +116,8 @@ __device__ __forceinline__ long long bfp_new_value(long long t, int S, int sout,
 // steps on the lines of class (py, pz), x parity pa first.  vmask: classes
 // holding valid z (others read as zero).  rc (nullable): fused residual +
 // injection into the FP64 right-hand side of level l+1 (runs of class (0,0)
-// ending on even x).  zout (nullable): FP64 copy of the updated lines.
+// ending on even x).  zout (nullable): FP64 copy of the updated lines; with
+// dpart, also the per-line partial sums of r.z (at [line], as the SpMV's p.Ap).
 // The work of block `blk` (warp wy of it) of a launch of k_gs_lines_bfp; COH:
 // load with L2-coherent loads (data written earlier in the same launch).
 // g1: the grid when count == 1 (a kernel parameter, so that a single grid's
@@ -126,7 +127,7 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
                                              int py, int pz, int pa, int steps, int vmask, const double *__restrict__ r,
                                              long long *__restrict__ zq, int *__restrict__ ze, const double *__restrict__ invd,
                                              const CgState *__restrict__ st, const Inst *__restrict__ tabc, double *__restrict__ rc,
-                                             const double *__restrict__ kap, double *__restrict__ zout) {
+                                             const double *__restrict__ kap, double *__restrict__ zout, double *__restrict__ dpart) {
   const int ii = count == 1 ? 0 : find_inst<4>(tab, count, blk);
   const Inst g = count == 1 ? g1 : tab[ii];
   const int done = st ? ld_line<COH>(&st[ii].done) : 0;  // tested once the first loads are issued
@@ -239,6 +240,7 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
         }
       }
       if (lane == 0) eg[li] = kBfpNaN;
+      if (zout && dpart && lane == 0) dpart[g.poff + li] = bfp_nan();
       if (rc) {
         const Inst gc = tabc[ii];
         const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
@@ -296,17 +298,26 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
     const unsigned mhi = __reduce_or_sync(kFull, (unsigned)(mag >> 32)), mlo = __reduce_or_sync(kFull, (unsigned)mag);
     const int lz = mhi ? __clz(mhi) : 32 + __clz(mlo);  // 64 for an all-zero line
     const int up = min(max(lz - 6, 0), sout - kFxMinE);
+    double rz = 0.0;  // r.z over the line (FP64 output runs)
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int xe = 64 * c + 2 * lane;
       if (xe < nx) {
         *reinterpret_cast<longlong2 *>(qg + rowbase + xe) =
             make_longlong2((long long)((unsigned long long)sE[c] << up), (long long)((unsigned long long)sO[c] << up));
-        if (zout)
-          *reinterpret_cast<double2 *>(zout + g.off + rowbase + xe) = make_double2(fx_to_double(sE[c], sout), fx_to_double(sO[c], sout));
+        if (zout) {
+          const double ze_ = fx_to_double(sE[c], sout), zo_ = fx_to_double(sO[c], sout);
+          *reinterpret_cast<double2 *>(zout + g.off + rowbase + xe) = make_double2(ze_, zo_);
+          rz += rE[c] * ze_ + rO[c] * zo_;
+        }
       }
     }
     if (lane == 0) eg[li] = sout - up;
+    if (zout && dpart) {  // per-line partial of r.z, fixed shuffle tree
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rz += __shfl_down_sync(kFull, rz, o);
+      if (lane == 0) dpart[g.poff + li] = rz;
+    }
     if (rc) {  // r - A z at the even points from the final values, exactly
       const Inst gc = tabc[ii];
       const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
@@ -333,10 +344,11 @@ __global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ t
                                                       int steps, int vmask, const double *__restrict__ r, long long *__restrict__ zq,
                                                       int *__restrict__ ze, const double *__restrict__ invd, const CgState *__restrict__ st,
                                                       const Inst *__restrict__ tabc, double *__restrict__ rc,
-                                                      const double *__restrict__ kap, double *__restrict__ zout, const Inst g1) {
+                                                      const double *__restrict__ kap, double *__restrict__ zout, double *__restrict__ dpart,
+                                                      const Inst g1) {
   pdl_enter();
   gs_bfp_block<NC, false>(blockIdx.x, threadIdx.y, tab, g1, count, lpc, zc, py, pz, pa, steps, vmask, r, zq, ze, invd, st, tabc, rc, kap,
-                          zout);
+                          zout, dpart);
 }
 
 // Refinement z_f <- z_f + R^T z_c on the block-floating-point vectors for
@@ -434,7 +446,7 @@ __device__ __forceinline__ void bfp_tail_runs(const BfpTailPlan &P, int l, const
         const int vb = base + w / L.lpc;
         if (vb < L.nblk_line)
           gs_bfp_block<NC, true>(vb, w % L.lpc, L.tab, L.g1, P.count, L.lpc, L.zc, run.cls & 1, (run.cls >> 1) & 1, run.pa, run.steps,
-                                 vmask, L.r, L.zq, L.ze, L.invd, st, rc ? L.tabnext : nullptr, rc, L.kap, nullptr);
+                                 vmask, L.r, L.zq, L.ze, L.invd, st, rc ? L.tabnext : nullptr, rc, L.kap, nullptr, nullptr);
       }
     }
     vmask |= 1 << run.cls;

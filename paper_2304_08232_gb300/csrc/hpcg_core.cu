@@ -737,20 +737,21 @@ static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s
 // zq (mantissas) and ze (line exponents).
 template <int NC>
 static void launch_gs_bfp(const LevelData &L, int count, int py, int pz, int pa, int steps, int vmask, const double *r, const double *invd,
-                          const CgState *st, const Inst *tabc, double *rc, const double *kap, double *zout, cudaStream_t s) {
+                          const CgState *st, const Inst *tabc, double *rc, const double *kap, double *zout, double *dpart,
+                          cudaStream_t s) {
   launch_k(k_gs_lines_bfp<NC>, dim3(L.tab.nblk_line), dim3(32, L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py,
-           pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, L.inst[0]);
+           pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart, L.inst[0]);
 }
 
 static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, int steps, const double *r, cudaStream_t s,
-                                  const CgState *st, int vmask, double *rc, double *zout) {
+                                  const CgState *st, int vmask, double *rc, double *zout, double *dpart = nullptr) {
   const LevelData &L = h->lv[l];
   const double *invd = invd_of<double>(L, h->has_kappa);
   const double *kap = kap_of<double>(L, h->has_kappa);
   const Inst *tabc = rc ? h->lv[l + 1].tab.inst : nullptr;
   switch (L.tab.nch2) {
 #define HPCG_BFP_CASE(N) \
-  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, s); break;
+  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, dpart, s); break;
     HPCG_BFP_CASE(1) HPCG_BFP_CASE(2) HPCG_BFP_CASE(3) HPCG_BFP_CASE(4) HPCG_BFP_CASE(5) HPCG_BFP_CASE(6)
 #undef HPCG_BFP_CASE
     default: return HPCG_ERR_UNSUPPORTED;
@@ -763,9 +764,9 @@ static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, in
 // into runs as in enqueue_smoother.  rc (nullable): residual + injection
 // fused into the last run, which for the symmetric smoother is class (0,0)
 // ending on even x.  zout (nullable): the FP64 z, written by the last run of
-// every line class.
+// every line class; with dpart also the per-line partials of r.z.
 static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps, cudaStream_t s, const CgState *st, bool from_zero,
-                                double *rc, double *zout) {
+                                double *rc, double *zout, double *dpart = nullptr) {
   const std::vector<int> seq = phase_sequence(sweeps, 1);
   std::vector<std::pair<int, int>> runs;  // (first colour, steps)
   for (size_t i = 0; i < seq.size();) {
@@ -782,7 +783,8 @@ static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps,
     const int last_parity = (steps & 1) ? (k & 1) : 1 - (k & 1);
     double *rc_here = (rc && i + 1 == runs.size()) ? rc : nullptr;
     if (steps < 2 || (rc_here && (cls != 0 || last_parity != 0))) return HPCG_ERR_UNSUPPORTED;
-    TRY(enqueue_line_steps_bfp(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, s, st, vmask, rc_here, last_of_class ? zout : nullptr));
+    TRY(enqueue_line_steps_bfp(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, s, st, vmask, rc_here, last_of_class ? zout : nullptr,
+                               last_of_class ? dpart : nullptr));
     prof_mark(PK_SMOOTH, l);
     vmask |= 1 << cls;
   }
@@ -819,20 +821,21 @@ static int enqueue_tail_bfp(hpcg_ctx *h, cudaStream_t s, const CgState *st) {
 }
 
 // Listing 1 on levels 0..L-1: r is the finest right-hand side (FP64), z the
-// FP64 result on the finest level.
-static int enqueue_vcycle_bfp(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st) {
+// FP64 result on the finest level; rz (nullable): per-line partials of r.z.
+static int enqueue_vcycle_bfp(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st, double *rz) {
   const int L = h->levels;
   const int first = h->bfp_tail_first > 0 ? h->bfp_tail_first : L;  // levels from `first` run in the cluster kernel
   for (int l = 0; l < first; ++l) {
     const bool coarsest = l == L - 1;
     TRY(enqueue_smoother_bfp(h, l, l == 0 ? r : h->lv[l].r, coarsest ? 1 : h->opt.pre_sweeps, s, st, true,
-                             coarsest ? nullptr : h->lv[l + 1].r, (coarsest && l == 0) ? z : nullptr));
+                             coarsest ? nullptr : h->lv[l + 1].r, (coarsest && l == 0) ? z : nullptr, (coarsest && l == 0) ? rz : nullptr));
     if (coarsest) break;
   }
   if (first < L) TRY(enqueue_tail_bfp(h, s, st));
   for (int l = (first < L ? first : L - 1) - 1; l >= 0; --l) {
     TRY(enqueue_prolong_bfp(h, l, s, st));                                                                  // z <- z + refine(z_c)
-    TRY(enqueue_smoother_bfp(h, l, l == 0 ? r : h->lv[l].r, h->opt.post_sweeps, s, st, false, nullptr, l == 0 ? z : nullptr));
+    TRY(enqueue_smoother_bfp(h, l, l == 0 ? r : h->lv[l].r, h->opt.post_sweeps, s, st, false, nullptr, l == 0 ? z : nullptr,
+                             l == 0 ? rz : nullptr));
   }
   return HPCG_OK;
 }
@@ -875,8 +878,11 @@ static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_
 
 // z = M r on level-0 FP64 vectors, in the handle's precision.  r32_current:
 // the FP32 copy of r (level-0 r32) is already up to date (the CG update wrote it).
+// rz (nullable) and *rz_done: the block-floating-point V-cycle also writes the
+// per-line partials of r.z into rz, and says so.
 static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t s, const CgState *st, bool r32_current = false,
-                          bool keep_z32 = false) {
+                          bool keep_z32 = false, double *rz = nullptr, bool *rz_done = nullptr) {
+  if (rz_done) *rz_done = false;
   if (h->opt.precision == HPCG_MIXED) {
     const LevelData &L0 = h->lv[0];
     if (!r32_current) {
@@ -897,8 +903,11 @@ static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t 
     }
     return HPCG_OK;
   }
-  if (h->use_bfp && h->tail_first <= 0 && ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(z)) & 15) == 0)
-    return enqueue_vcycle_bfp(h, r, z, s, st);
+  if (h->use_bfp && h->tail_first <= 0 && ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(z)) & 15) == 0) {
+    TRY(enqueue_vcycle_bfp(h, r, z, s, st, rz));
+    if (rz_done) *rz_done = rz != nullptr;
+    return HPCG_OK;
+  }
   double *rl[kMaxLevels], *zl[kMaxLevels];
   rl[0] = const_cast<double *>(r);
   zl[0] = z;
@@ -907,6 +916,43 @@ static int enqueue_vcycle(hpcg_ctx *h, const double *r, double *z, cudaStream_t 
     zl[l] = h->lv[l].z;
   }
   return enqueue_vcycle_t<double>(h, rl, zl, s, st);
+}
+
+// Finalisation of a reduction with one partial per x-line of the finest
+// level: across a cluster of kFinCluster blocks per instance when the GPU can
+// run it, else in one block per instance (k_finalize, stencil 2).
+template <int Kind>
+static int enqueue_finalize_lines(hpcg_ctx *h, cudaStream_t s) {
+  const LevelData &L0 = h->lv[0];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kFinCluster * h->count);
+  cfg.blockDim = dim3(kRedThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributeClusterDimension;
+  a[0].val.clusterDim.x = kFinCluster;
+  a[0].val.clusterDim.y = 1;
+  a[0].val.clusterDim.z = 1;
+  cfg.attrs = a;
+  cfg.numAttrs = 1;
+  if (h->fin_cluster_ok < 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_finalize_lines<Kind>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    h->fin_cluster_ok = n > 0 ? 1 : 0;
+  }
+  if (h->fin_cluster_ok) {
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_finalize_lines<Kind>, (const Inst *)L0.tab.inst, h->count, (const double *)h->part,
+                                             h->st, h->hist);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "k_finalize_lines (cluster launch)");
+    return HPCG_OK;
+  }
+  launch_k(k_finalize<Kind>, h->count, kFinThreads, 0, s, L0.tab.inst, h->count, h->part, 2, h->st, h->hist, nullptr);
+  CKL("k_finalize");
+  return HPCG_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -953,17 +999,23 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   }
   // z = M r; mixed precision leaves z in FP32 (level-0 z32), which the dot and
   // the p update read directly (r32 is kept current by the CG updates)
-  TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st, mixed, mixed));
-  if (mixed)
-    launch_k(k_dot_partial<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, (const float *)L0.z32, h->part,
-             h->st);
-  else
-    launch_k(k_dot_partial<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, (const double *)h->cg_z, h->part,
-             h->st);
-  CKL("k_dot_partial");
-  prof_mark(PK_DOT, 0);
-  launch_k(k_finalize<FIN_RTZ>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
-  CKL("k_finalize<RTZ>");
+  // (the block-floating-point V-cycle also leaves the per-line partials of r.z)
+  bool rz_fused = false;
+  TRY(enqueue_vcycle(h, h->cg_r, h->cg_z, s, h->st, mixed, mixed, h->part, &rz_fused));
+  if (rz_fused) {
+    TRY(enqueue_finalize_lines<FIN_RTZ>(h, s));
+  } else {
+    if (mixed)
+      launch_k(k_dot_partial<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, (const float *)L0.z32, h->part,
+               h->st);
+    else
+      launch_k(k_dot_partial<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_r, (const double *)h->cg_z,
+               h->part, h->st);
+    CKL("k_dot_partial");
+    prof_mark(PK_DOT, 0);
+    launch_k(k_finalize<FIN_RTZ>, h->count, kRedThreads, 0, s, L0.tab.inst, h->count, h->part, 0, h->st, h->hist, nullptr);
+    CKL("k_finalize<RTZ>");
+  }
   prof_mark(PK_FINALIZE, 0);
   if (mixed)
     launch_k(k_update_p<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const float *)L0.z32, h->cg_p, h->st);
@@ -973,8 +1025,12 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   prof_mark(PK_UPDATE, 0);
   TRY((enqueue_spmv<double, 0>(h, 0, h->cg_p, nullptr, h->cg_ap, kap, h->part, h->st, s)));  // Ap, p.Ap partials
   prof_mark(PK_SPMV, 0);
-  launch_k(k_finalize<FIN_PAP>, h->count, kFinThreads, 0, s, L0.tab.inst, h->count, h->part, L0.tab.nch ? 2 : 1, h->st, h->hist, nullptr);
-  CKL("k_finalize<PAP>");
+  if (L0.tab.nch) {
+    TRY(enqueue_finalize_lines<FIN_PAP>(h, s));
+  } else {
+    launch_k(k_finalize<FIN_PAP>, h->count, kFinThreads, 0, s, L0.tab.inst, h->count, h->part, 1, h->st, h->hist, nullptr);
+    CKL("k_finalize<PAP>");
+  }
   prof_mark(PK_FINALIZE, 0);
   launch_k(k_update_xr, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r,
            mixed ? L0.r32 : nullptr, h->part, h->st);

@@ -95,6 +95,7 @@ struct hpcg_ctx {
   int bfp_tail_first = -1;  // -1: none
   int bfp_tail_ok = -1;     // -1: not checked yet; 0: the GPU cannot run the cluster
   size_t o_tail_bfp = 0;    // BfpTailPlan
+  int fin_cluster_ok = -1;  // -1: not checked yet; 1: per-line reductions finalise in a cluster (k_finalize_lines)
   int device = 0;
   std::mutex mu;
 };

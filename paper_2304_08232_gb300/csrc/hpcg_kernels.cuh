@@ -9,6 +9,7 @@
 // one launch covers a whole batch; `st` (nullable) gates work per instance
 // once that instance's CG has converged.
 #pragma once
+#include <cooperative_groups.h>
 #include "hpcg_device.cuh"
 
 namespace hpcg {
@@ -253,6 +254,41 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const Inst *__restrict
     return;
   }
   fin_apply<Kind>(st[ii], s, hist ? hist + (long)ii * kHistoryCap : nullptr);
+}
+
+// k_finalize for one partial per x-line (the line SpMV's p.Ap, the V-cycle's
+// r.z) split over the kFinCluster blocks of one thread-block cluster per
+// instance: on one SM the FP64 adds of a 192^3 grid's 36,864 partials take
+// about 10 us.  Block k sums a fixed slice of the instance's lines, block 0
+// adds the slice sums in rank order (read from the other blocks' shared
+// memory) and updates the CG scalars, so the order of every addition is
+// fixed.  All blocks pass both cluster barriers (no early exit).
+constexpr int kFinCluster = 8;
+
+template <int Kind>
+__global__ void __launch_bounds__(kRedThreads) k_finalize_lines(const Inst *__restrict__ tab, int count, const double *__restrict__ partials,
+                                                                CgState *__restrict__ st, double *__restrict__ hist) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cluster = cgr::this_cluster();
+  __shared__ double sh[kRedThreads / 32];
+  __shared__ double slice_sum;
+  pdl_enter();
+  const int ii = blockIdx.x / kFinCluster;
+  const int k = (int)cluster.block_rank();
+  const Inst g = tab[ii];
+  const bool done = st[ii].done != 0;
+  const int cnt = g.ny * g.nz;
+  const int per = (cnt + kFinCluster - 1) / kFinCluster;
+  const int lo = min(cnt, k * per), hi = min(cnt, lo + per);
+  const double s = done ? 0.0 : sum_partials(partials, g.poff + lo, hi - lo, sh);
+  if (threadIdx.x == 0) slice_sum = s;
+  cluster.sync();
+  if (k == 0 && threadIdx.x == 0 && !done) {
+    double tot = 0.0;
+    for (int j = 0; j < kFinCluster; ++j) tot += *cluster.map_shared_rank(&slice_sum, j);
+    fin_apply<Kind>(st[ii], tot, hist ? hist + (long)ii * kHistoryCap : nullptr);
+  }
+  cluster.sync();
 }
 
 // p = z + beta p (p = z on the first iteration or after a restart); z in FP64
