@@ -357,7 +357,7 @@ def run_gpu(args):
     achieved_gbs = bytes_launch / (k_ms * 1e-3) / 1e9
     # DRAM traffic of one finest-level launch (post-smoother run [0,1]) from an
     # ncu capture at 192^3 (profiles/k_gs_lines_bfp_192cubed.md)
-    traffic = (71.032064e6 + 0.534016e6) if (NX, NY, NZ) == (192, 192, 192) else None
+    traffic = (71.048192e6 + 0.411392e6) if (NX, NY, NZ) == (192, 192, 192) else None
     roofline = {"bound": "hbm", "kernel": "k_gs_lines_bfp<3> (finest level, colour-pair runs of the V-cycle)",
                 "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
                 "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
