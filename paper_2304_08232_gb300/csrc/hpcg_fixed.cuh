@@ -206,13 +206,6 @@ __device__ __forceinline__ long long shr_fx(long long v, int d) { return d < 64 
 // to within one unit (the multiplier's relative excess is below 2^-63).
 constexpr unsigned long long kDiv26 = 11351842506898185610ULL;
 
-// (s 2^(S-1080)) / 26 as FP64 with one rounding: the quotient keeps four more
-// fraction bits than s (scale S - 4), then converts as fx_to_double does.
-__device__ __forceinline__ double fx_div26(long long s, int S) {
-  const unsigned long long a = s < 0 ? 0ULL - (unsigned long long)s : (unsigned long long)s;
-  const long long q = (long long)__umul64hi(a, kDiv26);
-  return fx_to_double(s < 0 ? -q : q, S - 4);
-}
 
 
 template <int NC>
