@@ -206,8 +206,6 @@ __device__ __forceinline__ long long shr_fx(long long v, int d) { return d < 64 
 // to within one unit (the multiplier's relative excess is below 2^-63).
 constexpr unsigned long long kDiv26 = 11351842506898185610ULL;
 
-
-
 template <int NC>
 __device__ __forceinline__ void prev_of_int(const int (&v)[NC], int (&out)[NC], int lane) {
 #pragma unroll
