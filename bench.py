@@ -336,11 +336,11 @@ def run_gpu(args):
         return 0
 
     # --- dominant kernel: the block-floating-point colour-pair kernel
-    # k_gs_lines_bfp on the finest level, as the FP64 solve runs it: every
-    # launch of one CG iteration is bracketed by CUDA events on the launching
-    # stream (hpcg_profile_iteration), 14 launches on the finest level (pre-
-    # and post-smoother, 7 runs each: [0,1] [2,3] [4,5] [6,7,6] [5,4] [3,2]
-    # [1,0]); the median of 5 iterations.
+    # k_gs_lines_bfp on the finest level, as the FP64 solve runs it: CUDA
+    # events on the launching stream bracket every kernel group of one CG
+    # iteration (hpcg_profile_iteration); the finest level's pre- and
+    # post-smoother are 14 launches of it (7 runs each: [0,1] [2,3] [4,5]
+    # [6,7,6] [5,4] [3,2] [1,0]); the median of 5 iterations.
     shapes = tuned_shapes(prob)
     peaks, peak_kind = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
@@ -363,7 +363,7 @@ def run_gpu(args):
                 "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
                 "bytes_algorithmic_per_launch": bytes_launch, "traffic": traffic,
                 "ms_per_launch": k_ms, "launches_timed": launches_l0,
-                "timing": "CUDA events around every launch of one CG iteration (hpcg_profile_iteration), median of 5",
+                "timing": "CUDA events around the finest level's two smoother applications (14 launches) of one CG iteration (hpcg_profile_iteration), median of 5",
                 "launch_shapes_per_level": shapes}
     # The FP64-storage colour kernel (k_gs_lines_fx: hpcg_rbgs, and the V-cycle
     # with block_fp = 0) for comparison: one symmetric sweep, 7 launches

@@ -668,10 +668,10 @@ static int enqueue_smoother(hpcg_ctx *h, int l, const T *r, T *z, int sweeps, cu
       if (fused) *fused = true;
     }
     TRY(enqueue_line_steps<T>(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, z, s, st, vmask, rc_here));
-    prof_mark(PK_SMOOTH, l);
     vmask |= 1 << cls;
     i = j;
   }
+  prof_mark(PK_SMOOTH, l);  // one event per smoother application: its runs keep their launch overlap
   return HPCG_OK;
 }
 
@@ -785,9 +785,9 @@ static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps,
     if (steps < 2 || (rc_here && (cls != 0 || last_parity != 0))) return HPCG_ERR_UNSUPPORTED;
     TRY(enqueue_line_steps_bfp(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, s, st, vmask, rc_here, last_of_class ? zout : nullptr,
                                last_of_class ? dpart : nullptr));
-    prof_mark(PK_SMOOTH, l);
     vmask |= 1 << cls;
   }
+  prof_mark(PK_SMOOTH, l);  // one event per smoother application: its runs keep their launch overlap
   return HPCG_OK;
 }
 
