@@ -194,7 +194,11 @@ static void plan(hpcg_ctx *h, const std::vector<int> &dims) {
     }
     L.n = rows;
     L.nlines = 0;
-    for (const Inst &g : L.inst) L.nlines += (long)g.ny * g.nz;
+    L.even_nx = true;
+    for (const Inst &g : L.inst) {
+      L.nlines += (long)g.ny * g.nz;
+      L.even_nx = L.even_nx && (g.nx % 2) == 0;
+    }
     L.tab.count = h->count;
     L.tab.nblk_full = bf;
     L.tab.nblk_half = bh;
@@ -597,6 +601,11 @@ static void launch_gs_lines(const LevelData &L, int count, int py, int pz, int p
                                                 st, tabc, rc, kap);
       return;
     }
+  }
+  if (L.even_nx && ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(z)) & (2 * sizeof(T) - 1)) == 0) {  // x pairs as vectors
+    launch_k(k_gs_lines<T, NCH, true>, grid, block, 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa, steps, vmask, r, z,
+             invd, st, tabc, rc, kap);
+    return;
   }
   launch_k(k_gs_lines<T, NCH>, grid, block, 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py, pz, pa, steps, vmask, r, z, invd, st,
                                             tabc, rc, kap);

@@ -18,6 +18,7 @@
 // values, and for a third step the first parity again.  Each step is the
 // update of Eq. 1, z_i <- (r_i + sum_{j != i} z_j) / A_ii.
 #pragma once
+#include <type_traits>
 #include "hpcg_device.cuh"
 
 namespace hpcg {
@@ -47,6 +48,16 @@ template <bool COH, typename T>
 __device__ __forceinline__ T ld_line(const T *p) {
   if (COH) return __ldcg(p);
   return __ldg(p);
+}
+
+// The values at x and x + 1 of a line (x even, line length even, so the pair
+// is aligned to its size) in one vector load.
+template <bool COH, typename T>
+__device__ __forceinline__ void ld_pair(const T *p, T &e, T &o) {
+  using V = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  const V v = ld_line<COH>(reinterpret_cast<const V *>(p));
+  e = v.x;
+  o = v.y;
 }
 
 // Line class of line (y, z): its y and z parities, (y & 1) + 2 (z & 1).
@@ -104,7 +115,7 @@ __device__ __forceinline__ void next_of(const T (&v)[NC], T (&out)[NC], int lane
 }
 
 // Sum over y-1, y, y+1 of line (., y, zz) at even (te) and odd (to) x.
-template <typename T, int NC, bool COH>
+template <typename T, int NC, bool COH, bool PAIR = false>
 __device__ __forceinline__ void tsum2(const T *__restrict__ zg, int nx, int ny, int nz, int y, int zz, int lane, T (&te)[NC],
                                       T (&to)[NC], int vmask) {
   const bool zin = zz >= 0 && zz < nz;
@@ -119,10 +130,21 @@ __device__ __forceinline__ void tsum2(const T *__restrict__ zg, int nx, int ny, 
   for (int c = 0; c < NC; ++c) {
     const int xe = 2 * (lane + 32 * c), xo = xe + 1;
     T se = T(0), so = T(0);
-    if (xe < nx)
-      se = ((ym ? ld_line<COH>(lm + xe) : T(0)) + (y0 ? ld_line<COH>(l0 + xe) : T(0))) + (yp ? ld_line<COH>(lp + xe) : T(0));
-    if (xo < nx)
-      so = ((ym ? ld_line<COH>(lm + xo) : T(0)) + (y0 ? ld_line<COH>(l0 + xo) : T(0))) + (yp ? ld_line<COH>(lp + xo) : T(0));
+    if (PAIR) {
+      if (xe < nx) {
+        T ae = T(0), ao = T(0), be = T(0), bo = T(0), de = T(0), d_o = T(0);
+        if (ym) ld_pair<COH>(lm + xe, ae, ao);
+        if (y0) ld_pair<COH>(l0 + xe, be, bo);
+        if (yp) ld_pair<COH>(lp + xe, de, d_o);
+        se = (ae + be) + de;
+        so = (ao + bo) + d_o;
+      }
+    } else {
+      if (xe < nx)
+        se = ((ym ? ld_line<COH>(lm + xe) : T(0)) + (y0 ? ld_line<COH>(l0 + xe) : T(0))) + (yp ? ld_line<COH>(lp + xe) : T(0));
+      if (xo < nx)
+        so = ((ym ? ld_line<COH>(lm + xo) : T(0)) + (y0 ? ld_line<COH>(l0 + xo) : T(0))) + (yp ? ld_line<COH>(lp + xo) : T(0));
+    }
     te[c] = se;
     to[c] = so;
   }
@@ -138,7 +160,8 @@ __device__ __forceinline__ void tsum2(const T *__restrict__ zg, int nx, int ny, 
 // ends on even x: every injected fine row (2xc, 2yc, 2zc) lies on these lines,
 // its neighbour sum is P + z(x-1) + z(x+1) with values final for this
 // smoother application, so rc[c] = r - (A_ii z - that sum) is formed here.
-template <typename T, int NC, bool COH = false>
+// PAIR: every line has an even length, so x pairs move as one vector.
+template <typename T, int NC, bool COH = false, bool PAIR = false>
 __device__ __forceinline__ void gs_lines_vblock(int blk, int wy, const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz,
                                                 int pa, int steps, int vmask, const T *__restrict__ r, T *__restrict__ z,
                                                 const T *__restrict__ invd, const CgState *__restrict__ st,
@@ -163,11 +186,29 @@ __device__ __forceinline__ void gs_lines_vblock(int blk, int wy, const Inst *__r
   const bool ym = y - 1 >= 0 && ((vmask >> cls_v) & 1), yp = y + 1 < g.ny && ((vmask >> cls_v) & 1);
   const bool own_valid = (vmask >> line_class(y, pz)) & 1;
   T tpe[NC], tpo[NC];
-  tsum2<T, NC, COH>(zg, nx, g.ny, g.nz, y, 2 * m0 + pz - 1, lane, tpe, tpo, vmask);
+  tsum2<T, NC, COH, PAIR>(zg, nx, g.ny, g.nz, y, 2 * m0 + pz - 1, lane, tpe, tpo, vmask);
   for (int m = m0; m < m1; ++m) {
     const int zz = 2 * m + pz;
     T tne[NC], tno[NC], PE[NC], PO[NC];
-    tsum2<T, NC, COH>(zg, nx, g.ny, g.nz, y, zz + 1, lane, tne, tno, vmask);
+    tsum2<T, NC, COH, PAIR>(zg, nx, g.ny, g.nz, y, zz + 1, lane, tne, tno, vmask);
+    const long rowbase = (long)zz * sxy + (long)y * nx;
+    T E[NC], O[NC], rE[NC], rO[NC];
+    if (PAIR) {  // own line and right-hand side, issued with the neighbours' loads
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 2 * (lane + 32 * c);
+        E[c] = O[c] = rE[c] = rO[c] = T(0);
+        if (xe < nx) {
+          if (own_valid) {
+            if (COH)
+              ld_pair<true>(zg + rowbase + xe, E[c], O[c]);
+            else
+              ld_pair<false>(zg + rowbase + xe, E[c], O[c]);  // own line: this warp alone writes it
+          }
+          ld_pair<COH>(rg + rowbase + xe, rE[c], rO[c]);
+        }
+      }
+    }
     {
       T ce[NC], co[NC], sh[NC];
       const T *lm = zg + (long)zz * sxy + (long)(y - 1) * nx;
@@ -176,8 +217,18 @@ __device__ __forceinline__ void gs_lines_vblock(int blk, int wy, const Inst *__r
       for (int c = 0; c < NC; ++c) {
         const int xe = 2 * (lane + 32 * c), xo = xe + 1;
         T ve = T(0), vo = T(0);
-        if (xe < nx) ve = (ym ? ld_line<COH>(lm + xe) : T(0)) + (yp ? ld_line<COH>(lp + xe) : T(0));
-        if (xo < nx) vo = (ym ? ld_line<COH>(lm + xo) : T(0)) + (yp ? ld_line<COH>(lp + xo) : T(0));
+        if (PAIR) {
+          if (xe < nx) {
+            T ae = T(0), ao = T(0), de = T(0), d_o = T(0);
+            if (ym) ld_pair<COH>(lm + xe, ae, ao);
+            if (yp) ld_pair<COH>(lp + xe, de, d_o);
+            ve = ae + de;
+            vo = ao + d_o;
+          }
+        } else {
+          if (xe < nx) ve = (ym ? ld_line<COH>(lm + xe) : T(0)) + (yp ? ld_line<COH>(lp + xe) : T(0));
+          if (xo < nx) vo = (ym ? ld_line<COH>(lm + xo) : T(0)) + (yp ? ld_line<COH>(lp + xo) : T(0));
+        }
         ce[c] = (tpe[c] + tne[c]) + ve;  // off-line column sums at x
         co[c] = (tpo[c] + tno[c]) + vo;
       }
@@ -188,15 +239,15 @@ __device__ __forceinline__ void gs_lines_vblock(int blk, int wy, const Inst *__r
 #pragma unroll
       for (int c = 0; c < NC; ++c) PO[c] = (ce[c] + co[c]) + sh[c];
     }
-    const long rowbase = (long)zz * sxy + (long)y * nx;
-    T E[NC], O[NC], rE[NC], rO[NC];
+    if (!PAIR) {
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int xe = 2 * (lane + 32 * c), xo = xe + 1;
-      E[c] = (xe < nx && own_valid) ? (COH ? __ldcg(zg + rowbase + xe) : zg[rowbase + xe]) : T(0);
-      O[c] = (xo < nx && own_valid) ? (COH ? __ldcg(zg + rowbase + xo) : zg[rowbase + xo]) : T(0);
-      rE[c] = xe < nx ? (COH ? __ldcg(rg + rowbase + xe) : rg[rowbase + xe]) : T(0);
-      rO[c] = xo < nx ? (COH ? __ldcg(rg + rowbase + xo) : rg[rowbase + xo]) : T(0);
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 2 * (lane + 32 * c), xo = xe + 1;
+        E[c] = (xe < nx && own_valid) ? (COH ? __ldcg(zg + rowbase + xe) : zg[rowbase + xe]) : T(0);
+        O[c] = (xo < nx && own_valid) ? (COH ? __ldcg(zg + rowbase + xo) : zg[rowbase + xo]) : T(0);
+        rE[c] = xe < nx ? (COH ? __ldcg(rg + rowbase + xe) : rg[rowbase + xe]) : T(0);
+        rO[c] = xo < nx ? (COH ? __ldcg(rg + rowbase + xo) : rg[rowbase + xo]) : T(0);
+      }
     }
     T nb[NC];  // neighbours along x of the parity updated last
     for (int s = 0; s < steps; ++s) {
@@ -228,8 +279,13 @@ __device__ __forceinline__ void gs_lines_vblock(int blk, int wy, const Inst *__r
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int xe = 2 * (lane + 32 * c), xo = xe + 1;
-      if (write_e && xe < nx) zg[rowbase + xe] = E[c];
-      if (write_o && xo < nx) zg[rowbase + xo] = O[c];
+      if (PAIR && write_e && write_o) {
+        using V = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        if (xe < nx) *reinterpret_cast<V *>(zg + rowbase + xe) = V{E[c], O[c]};
+      } else {
+        if (write_e && xe < nx) zg[rowbase + xe] = E[c];
+        if (write_o && xo < nx) zg[rowbase + xo] = O[c];
+      }
     }
     if (rc) {
       // the last step updated even x; nb holds its (unchanged) left odd neighbours
@@ -253,13 +309,14 @@ __device__ __forceinline__ void gs_lines_vblock(int blk, int wy, const Inst *__r
   }
 }
 
-template <typename T, int NC>
+template <typename T, int NC, bool PAIR = false>
 __global__ void __launch_bounds__(256) k_gs_lines(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
                                                   int steps, int vmask, const T *__restrict__ r, T *__restrict__ z,
                                                   const T *__restrict__ invd, const CgState *__restrict__ st, const Inst *__restrict__ tabc,
                                                   T *__restrict__ rc, const T *__restrict__ kap) {
   pdl_enter();
-  gs_lines_vblock<T, NC>(blockIdx.x, threadIdx.y, tab, count, lpc, zc, py, pz, pa, steps, vmask, r, z, invd, st, tabc, rc, kap);
+  gs_lines_vblock<T, NC, false, PAIR>(blockIdx.x, threadIdx.y, tab, count, lpc, zc, py, pz, pa, steps, vmask, r, z, invd, st, tabc, rc,
+                                      kap);
 }
 
 // y = A x (Mode 0) or y = b - A x (Mode 1) over every x-line; A x = (27 + kappa) x - S
