@@ -118,6 +118,8 @@ __device__ __forceinline__ long long bfp_new_value(long long t, int S, int sout,
 // injection into the FP64 right-hand side of level l+1 (runs of class (0,0)
 // ending on even x).  zout (nullable): FP64 copy of the updated lines; with
 // dpart, also the per-line partial sums of r.z (at [line], as the SpMV's p.Ap).
+// zqc, zec, tabcp (nullable): the next coarser level's z and table, whose
+// refinement into these (class (0,0)) lines is fused into this run.
 // The work of block `blk` (warp wy of it) of a launch of k_gs_lines_bfp; COH:
 // load with L2-coherent loads (data written earlier in the same launch).
 // g1: the grid when count == 1 (a kernel parameter, so that a single grid's
@@ -127,7 +129,9 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
                                              int py, int pz, int pa, int steps, int vmask, const double *__restrict__ r,
                                              long long *__restrict__ zq, int *__restrict__ ze, const double *__restrict__ invd,
                                              const CgState *__restrict__ st, const Inst *__restrict__ tabc, double *__restrict__ rc,
-                                             const double *__restrict__ kap, double *__restrict__ zout, double *__restrict__ dpart) {
+                                             const double *__restrict__ kap, double *__restrict__ zout, double *__restrict__ dpart,
+                                             const long long *__restrict__ zqc, const int *__restrict__ zec,
+                                             const Inst *__restrict__ tabcp) {
   const int ii = count == 1 ? 0 : find_inst<4>(tab, count, blk);
   const Inst g = count == 1 ? g1 : tab[ii];
   const int done = st ? ld_line<COH>(&st[ii].done) : 0;  // tested once the first loads are issued
@@ -170,7 +174,7 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
     const long rowbase = (long)zz * sxy + (long)y * nx;
     const int eu = ym ? ld_line<COH>(eg + li - 1) : kFxMinE;
     const int ew = yp ? ld_line<COH>(eg + li + 1) : kFxMinE;
-    const int eo = own_valid ? (COH ? __ldcg(eg + li) : eg[li]) : kFxMinE;
+    int eo = own_valid ? (COH ? __ldcg(eg + li) : eg[li]) : kFxMinE;
     long long ue[NC], uo[NC], we[NC], wo[NC], qe[NC], qo[NC];
     ld_pairs_q<NC, COH>(qg + rowbase - nx, ym, nx, lane, ue, uo);
     ld_pairs_q<NC, COH>(qg + rowbase + nx, yp, nx, lane, we, wo);
@@ -184,6 +188,24 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
         qe[c] = v.x;
         qo[c] = v.y;
       }
+    }
+    if (zqc) {
+      // refinement z <- z + R^T z_c fused into this run (the first of the
+      // post-smoother, on class (0,0) lines): coarse line (y/2, zz/2) adds to
+      // the even x of this line, which moves to exponent max(e_f, e_c) + 1
+      // (the arithmetic of prolong_bfp_line, in registers)
+      const Inst gc = tabcp[ii];
+      const long lic = (long)(zz >> 1) * gc.ny + (y >> 1);
+      const int e_c = ld_line<COH>(zec + gc.poff + lic);
+      const int Sp = max(eo, e_c) + 1;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int xe = 64 * c + 2 * lane;
+        const long long cv = xe < nx ? ld_line<COH>(zqc + gc.off + lic * gc.nx + (xe >> 1)) : 0;
+        qe[c] = shr_q(qe[c], Sp - eo) + shr_q(cv, Sp - e_c);
+        qo[c] = shr_q(qo[c], Sp - eo);
+      }
+      eo = (eo > kFxMaxE || e_c > kFxMaxE) ? kBfpNaN : Sp;
     }
     double rE[NC], rO[NC];
     ld_pairs_d<NC, COH>(rg + rowbase, nx, lane, rE, rO);
@@ -345,16 +367,19 @@ __global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ t
                                                       int *__restrict__ ze, const double *__restrict__ invd, const CgState *__restrict__ st,
                                                       const Inst *__restrict__ tabc, double *__restrict__ rc,
                                                       const double *__restrict__ kap, double *__restrict__ zout, double *__restrict__ dpart,
-                                                      const Inst g1) {
+                                                      const long long *__restrict__ zqc, const int *__restrict__ zec,
+                                                      const Inst *__restrict__ tabcp, const Inst g1) {
   pdl_enter();
   gs_bfp_block<NC, false>(blockIdx.x, threadIdx.y, tab, g1, count, lpc, zc, py, pz, pa, steps, vmask, r, zq, ze, invd, st, tabc, rc, kap,
-                          zout, dpart);
+                          zout, dpart, zqc, zec, tabcp);
 }
 
 // Refinement z_f <- z_f + R^T z_c on the block-floating-point vectors for
 // coarse line wl (all instances' lines numbered in order), which feeds the
 // even points of fine line (2 yc, 2 zc).  The fine line moves to exponent
-// max(e_f, e_c) + 1, which keeps the sums below 2^58.
+// max(e_f, e_c) + 1, which keeps the sums below 2^58.  (The cluster kernel's
+// refinement step; the per-launch V-cycle does the same inside the first
+// post-smoother run.)
 template <bool COH>
 __device__ __forceinline__ void prolong_bfp_line(int wl, int lane, const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count,
                                                  const long long *__restrict__ qc, const int *__restrict__ ec, long long *__restrict__ qf,
@@ -381,14 +406,6 @@ __device__ __forceinline__ void prolong_bfp_line(int wl, int lane, const Inst *_
   if (lane == 0) ef[gf.poff + lf] = bad ? kBfpNaN : S;
 }
 
-// One launch: one warp per coarse line of every instance.
-__global__ void __launch_bounds__(256) k_prolong_bfp(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count, int nlines,
-                                                     const long long *__restrict__ qc, const int *__restrict__ ec,
-                                                     long long *__restrict__ qf, int *__restrict__ ef, const CgState *__restrict__ st) {
-  pdl_enter();
-  const int wl = blockIdx.x * blockDim.y + threadIdx.y;
-  if (wl < nlines) prolong_bfp_line<false>(wl, threadIdx.x, tabf, tabc, count, qc, ec, qf, ef, st);
-}
 
 // ---------------------------------------------------------------------------
 // The coarse end of the V-cycle in one launch of one thread-block cluster.
@@ -402,7 +419,7 @@ __global__ void __launch_bounds__(256) k_prolong_bfp(const Inst *__restrict__ ta
 // separated by the cluster's hardware barrier (release/acquire at cluster
 // scope); data written earlier in the launch is read with L2-coherent loads.
 // Every block executes the same barrier sequence, so the barrier always
-// completes.  The arithmetic is that of k_gs_lines_bfp / k_prolong_bfp, so
+// completes.  The arithmetic is that of k_gs_lines_bfp / prolong_bfp_line, so
 // the results are the same bits as one launch per run.
 constexpr int kBfpTailCtas = 16;
 constexpr int kBfpTailWarps = 16;  // warps per block of the cluster kernel
@@ -446,7 +463,8 @@ __device__ __forceinline__ void bfp_tail_runs(const BfpTailPlan &P, int l, const
         const int vb = base + w / L.lpc;
         if (vb < L.nblk_line)
           gs_bfp_block<NC, true>(vb, w % L.lpc, L.tab, L.g1, P.count, L.lpc, L.zc, run.cls & 1, (run.cls >> 1) & 1, run.pa, run.steps,
-                                 vmask, L.r, L.zq, L.ze, L.invd, st, rc ? L.tabnext : nullptr, rc, L.kap, nullptr, nullptr);
+                                 vmask, L.r, L.zq, L.ze, L.invd, st, rc ? L.tabnext : nullptr, rc, L.kap, nullptr, nullptr, nullptr,
+                                 nullptr, nullptr);
       }
     }
     vmask |= 1 << run.cls;

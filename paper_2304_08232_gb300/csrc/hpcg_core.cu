@@ -747,20 +747,24 @@ static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s
 template <int NC>
 static void launch_gs_bfp(const LevelData &L, int count, int py, int pz, int pa, int steps, int vmask, const double *r, const double *invd,
                           const CgState *st, const Inst *tabc, double *rc, const double *kap, double *zout, double *dpart,
-                          cudaStream_t s) {
+                          const LevelData *C, cudaStream_t s) {
   launch_k(k_gs_lines_bfp<NC>, dim3(L.tab.nblk_line), dim3(32, L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py,
-           pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart, L.inst[0]);
+           pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart, C ? (const long long *)C->zq : nullptr,
+           C ? (const int *)C->ze : nullptr, C ? C->tab.inst : nullptr, L.inst[0]);
 }
 
+// prolong (nullable): refine from this coarser level, fused into the run (a
+// class (0,0) run of a post-smoother).
 static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, int steps, const double *r, cudaStream_t s,
-                                  const CgState *st, int vmask, double *rc, double *zout, double *dpart = nullptr) {
+                                  const CgState *st, int vmask, double *rc, double *zout, double *dpart = nullptr,
+                                  const LevelData *prolong = nullptr) {
   const LevelData &L = h->lv[l];
   const double *invd = invd_of<double>(L, h->has_kappa);
   const double *kap = kap_of<double>(L, h->has_kappa);
   const Inst *tabc = rc ? h->lv[l + 1].tab.inst : nullptr;
   switch (L.tab.nch2) {
 #define HPCG_BFP_CASE(N) \
-  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, dpart, s); break;
+  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, dpart, prolong, s); break;
     HPCG_BFP_CASE(1) HPCG_BFP_CASE(2) HPCG_BFP_CASE(3) HPCG_BFP_CASE(4) HPCG_BFP_CASE(5) HPCG_BFP_CASE(6)
 #undef HPCG_BFP_CASE
     default: return HPCG_ERR_UNSUPPORTED;
@@ -773,9 +777,12 @@ static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, in
 // into runs as in enqueue_smoother.  rc (nullable): residual + injection
 // fused into the last run, which for the symmetric smoother is class (0,0)
 // ending on even x.  zout (nullable): the FP64 z, written by the last run of
-// every line class; with dpart also the per-line partials of r.z.
+// every line class; with dpart also the per-line partials of r.z.  refine:
+// the refinement from level l+1 (Listing 1's z <- z + refine(z_c)) is fused
+// into the first run, which for the symmetric smoother is class (0,0): the
+// lines that hold every injected point.
 static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps, cudaStream_t s, const CgState *st, bool from_zero,
-                                double *rc, double *zout, double *dpart = nullptr) {
+                                double *rc, double *zout, double *dpart = nullptr, bool refine = false) {
   const std::vector<int> seq = phase_sequence(sweeps, 1);
   std::vector<std::pair<int, int>> runs;  // (first colour, steps)
   for (size_t i = 0; i < seq.size();) {
@@ -792,22 +799,16 @@ static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps,
     const int last_parity = (steps & 1) ? (k & 1) : 1 - (k & 1);
     double *rc_here = (rc && i + 1 == runs.size()) ? rc : nullptr;
     if (steps < 2 || (rc_here && (cls != 0 || last_parity != 0))) return HPCG_ERR_UNSUPPORTED;
+    const bool refine_here = refine && i == 0;
+    if (refine_here && cls != 0) return HPCG_ERR_UNSUPPORTED;
     TRY(enqueue_line_steps_bfp(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, s, st, vmask, rc_here, last_of_class ? zout : nullptr,
-                               last_of_class ? dpart : nullptr));
+                               last_of_class ? dpart : nullptr, refine_here ? &h->lv[l + 1] : nullptr));
     vmask |= 1 << cls;
   }
   prof_mark(PK_SMOOTH, l);  // one event per smoother application: its runs keep their launch overlap
   return HPCG_OK;
 }
 
-static int enqueue_prolong_bfp(hpcg_ctx *h, int l, cudaStream_t s, const CgState *st) {
-  const LevelData &F = h->lv[l], &C = h->lv[l + 1];
-  launch_k(k_prolong_bfp, dim3((unsigned)((C.nlines + 7) / 8)), dim3(32, 8), 0, s, F.tab.inst, C.tab.inst, h->count, (int)C.nlines,
-           (const long long *)C.zq, (const int *)C.ze, F.zq, F.ze, st);
-  CKL("k_prolong_bfp");
-  prof_mark(PK_PROLONG, l);
-  return HPCG_OK;
-}
 
 // Levels bfp_tail_first..L-1 of the V-cycle in one cluster launch.
 static int enqueue_tail_bfp(hpcg_ctx *h, cudaStream_t s, const CgState *st) {
@@ -842,9 +843,9 @@ static int enqueue_vcycle_bfp(hpcg_ctx *h, const double *r, double *z, cudaStrea
   }
   if (first < L) TRY(enqueue_tail_bfp(h, s, st));
   for (int l = (first < L ? first : L - 1) - 1; l >= 0; --l) {
-    TRY(enqueue_prolong_bfp(h, l, s, st));                                                                  // z <- z + refine(z_c)
+    // z <- z + refine(z_c), fused into the post-smoother's first run, then post-smoothing
     TRY(enqueue_smoother_bfp(h, l, l == 0 ? r : h->lv[l].r, h->opt.post_sweeps, s, st, false, nullptr, l == 0 ? z : nullptr,
-                             l == 0 ? rz : nullptr));
+                             l == 0 ? rz : nullptr, true));
   }
   return HPCG_OK;
 }
