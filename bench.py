@@ -347,13 +347,18 @@ def run_gpu(args):
     l0_ms = sorted(prob.profile_iteration(b)["smoother_ms"][0] for _ in range(5))[2]
     launches_l0 = 7 * 2
     k_ms = l0_ms / launches_l0
-    # Per launch it must read z of every line (the off-line neighbours of a
-    # class are the other three classes, plus its own line: 8 n bytes of int64
-    # mantissas), r of its class lines (2 n) and write its class lines (2 n):
-    # 12 n bytes.  It issues no FP64 instruction without kappa (the division by
-    # 26 is an integer multiply-high), so HBM bounds it: 12 n / HBM = 12.5 us
-    # at 192^3.
-    bytes_launch = 12 * n
+    # Algorithmic bytes of the 14 launches (int64 mantissas of z, FP64 r):
+    # a full run reads z of every line (the off-line neighbours of a class are
+    # the other three classes, plus its own line: 8 n), r of its class lines
+    # (2 n) and writes its class lines (2 n): 12 n.  The pre-smoother starts
+    # from z = 0 and reads only the classes already written: [0,1] 4 n,
+    # [2,3] 6 n, [4,5] 8 n, [6,7,6] 10 n, then 3 x 12 n, + n for the restricted
+    # residual it writes; the post-smoother's first run also reads the coarse
+    # z (n), and its last run of each class writes z in FP64 (4 x 2 n).
+    # Total 158 n, 11.3 n per launch on average.  No FP64 instruction without
+    # kappa (the division by 26 is an integer multiply-high): HBM bounds it,
+    # 11.3 n / HBM = 11.8 us per launch at 192^3.
+    bytes_launch = 158 * n / launches_l0
     achieved_gbs = bytes_launch / (k_ms * 1e-3) / 1e9
     # DRAM traffic of one finest-level launch (post-smoother run [0,1]) from an
     # ncu capture at 192^3 (profiles/k_gs_lines_bfp_192cubed.md)
@@ -362,6 +367,7 @@ def run_gpu(args):
                 "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
                 "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
                 "bytes_algorithmic_per_launch": bytes_launch, "traffic": traffic,
+                "bytes_basis": "158 n per V-cycle over the 14 finest-level launches (12 n per full run)",
                 "ms_per_launch": k_ms, "launches_timed": launches_l0,
                 "timing": "CUDA events around the finest level's two smoother applications (14 launches) of one CG iteration (hpcg_profile_iteration), median of 5",
                 "launch_shapes_per_level": shapes}
@@ -382,7 +388,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     sweep_ms = k0.elapsed_time(k1) / reps
     roofline["fp64_storage_kernel"] = {"kernel": "k_gs_lines_fx<3>", "ms_per_launch": sweep_ms / 7,
-                                       "achieved_gbs": bytes_launch / (sweep_ms / 7 * 1e-3) / 1e9,
+                                       "achieved_gbs": 12 * n / (sweep_ms / 7 * 1e-3) / 1e9,
                                        "fp64_instr_per_updated_row": 4}
     del r, z
     # SpMV line kernel (secondary): 7 + 4/zc FP64 instructions per row
