@@ -235,6 +235,45 @@ def other_forms(dev, stream):
     return res
 
 
+def hpcg_checks(prob, dev, stream):
+    """The benchmark flow around the solver that HPCG runs (Section II-D): the
+    symmetry test of A and of the preconditioner M, |x'Ay - y'Ax| and
+    |x'My - y'Mx| for random x, y in units of eps ||x|| ||y|| ||A||_inf
+    (||A||_inf = 52; for M the bound 1/26 of a Jacobi step stands in), and a
+    smoother study: time and iterations to 1e-9 of the symmetric smoother with
+    one and two sweeps and of the forward-only ablation (b = A x_true,
+    x_true ~ U[-1,1], seed 1)."""
+    import torch
+    from hpcg_inputs import mixed_precision_xtrue, normal
+    from paper_2304_08232_gb300 import HpcgProblem
+    n = NX * NY * NZ
+    eps = 2.0 ** -52
+    x = torch.as_tensor(normal(n, 41), device=dev)
+    y = torch.as_tensor(normal(n, 42), device=dev)
+    nx_, ny_ = float(torch.linalg.norm(x)), float(torch.linalg.norm(y))
+    dA = abs(float(torch.dot(x, prob.spmv(y))) - float(torch.dot(y, prob.spmv(x))))
+    dM = abs(float(torch.dot(x, prob.mg_vcycle(y))) - float(torch.dot(y, prob.mg_vcycle(x))))
+    sym = {"A_departure_eps": dA / (eps * nx_ * ny_ * 52.0), "M_departure_eps": dM / (eps * nx_ * ny_ / 26.0)}
+    xt = torch.as_tensor(mixed_precision_xtrue(n, seed=1), device=dev)
+    bt = prob.spmv(xt)
+    study = {}
+    for name, kw in [("symmetric_1_sweep", {}), ("symmetric_2_sweeps", {"pre_sweeps": 2, "post_sweeps": 2}),
+                     ("forward_only_1_sweep", {"symmetric": False})]:
+        p = HpcgProblem(NX, NY, NZ, levels=LEVELS, device=dev, **kw)
+        xs, st = p.pcg_solve(bt, max_iters=400, tol=1e-9)  # warm-up, graph capture
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xs, st = p.pcg_solve(bt, max_iters=400, tol=1e-9)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        study[name] = {"ms": e0.elapsed_time(e1), "iters": st.iters, "converged": st.converged,
+                       "err_vs_xtrue": float((xs - xt).abs().max() / xt.abs().max())}
+        del p, xs
+    return {"symmetry": sym, "smoother_study_to_1e-9": study}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -457,6 +496,7 @@ def run_gpu(args):
     breakdown = {"fp64": time_breakdown(prob, b), "mixed": time_breakdown(
         HpcgProblem(NX, NY, NZ, levels=LEVELS, precision="mixed", device=dev), b)}
     forms = {} if args.skip_forms else other_forms(dev, stream)
+    checks = {} if args.skip_forms else hpcg_checks(prob, dev, stream)
 
     # --- end to end through the public API with host buffers
     b_h = b.cpu().pin_memory()
@@ -514,6 +554,7 @@ def run_gpu(args):
         "iteration_breakdown": breakdown,
         "fp64_solve_variants": variants,
         "forms": forms,
+        "hpcg_checks": checks,
         "e2e": e2e,
         "clocks": clocks,
         "cpu_baseline": cpu,
