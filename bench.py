@@ -123,6 +123,38 @@ def dist_env():
     return world, rank, local
 
 
+def init_ranks(world, backend="nccl"):
+    """One process per GPU, rendezvous from MASTER_ADDR/MASTER_PORT.  The
+    replicas exchange nothing on the data path: the process group carries only
+    the barriers around the timed region and the max-over-ranks of the times."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+
+
+def rank_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(values, world, device="cpu"):
+    """Each value's maximum over the ranks: the slowest replica sets the job's time."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu().tolist()]
+
+
+def whole_job_gflops(world, flops_per_step, ms_per_step):
+    """Whole-job throughput: every replica did flops_per_step in ms_per_step
+    (the max over ranks)."""
+    return world * flops_per_step / (ms_per_step * 1e-3) / 1e9
+
+
 def time_breakdown(prob, b):
     """Per-level time of one CG iteration, as the paper's Figs. 4-7 (smoother
     vs restriction/refinement per level, MG vs CG): kernels launched one by one
@@ -310,9 +342,7 @@ def run_gpu(args):
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    init_ranks(world, "nccl")
     from hpcg_inputs import mixed_precision_xtrue
     from paper_2304_08232_gb300 import HpcgProblem, launch_count
 
@@ -334,9 +364,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        rank_barrier(world)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -355,14 +383,10 @@ def run_gpu(args):
     launches = launch_count() - l0
     ms = e0.elapsed_time(e1) / args.steps
     clocks = sampler.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([ms], world, dev)[0]
 
     flops_iter = hpcg_flops_per_iter(NX, NY, NZ, LEVELS)
-    value = world * flops_iter * ITERS / (ms * 1e-3) / 1e9
+    value = whole_job_gflops(world, flops_iter * ITERS, ms)
     # correctness of the timed solve: exact solution is ones
     err_ones = float((x - 1.0).abs().max().item())
 
@@ -521,8 +545,8 @@ def run_gpu(args):
         e2e_step()
     q1.record(stream)
     torch.cuda.synchronize()
-    e_ms = q0.elapsed_time(q1) / e_steps
-    e2e = {"value": world * flops_iter * ITERS / (e_ms * 1e-3) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": 2 * n * 8,
+    e_ms = max_over_ranks([q0.elapsed_time(q1) / e_steps], world, dev)[0]
+    e2e = {"value": whole_job_gflops(world, flops_iter * ITERS, e_ms), "unit": "GFLOP/s", "h2d_bytes_per_step": 2 * n * 8,
            "d2h_bytes_per_step": n * 8, "ms_per_step": e_ms}
 
     if world > 1:
