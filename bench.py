@@ -267,6 +267,57 @@ def other_forms(dev, stream):
     return res
 
 
+def ell_study(b, x_ref, dev, stream):
+    """The operator materialised as a sliced-ELL matrix (FP64 values, int32
+    columns, 27 slots per row in slices of 32), rows grouped by colour
+    (P^T A P, Section III-A) or in natural order: the same 50-iteration FP64
+    solve as the headline, the level-0 SpMV kernel against its algorithmic
+    bytes, and one level-0 smoother application (16 colour phases)."""
+    import torch
+    from paper_2304_08232_gb300 import HpcgEll
+    peak = measured_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS)
+    n = NX * NY * NZ
+
+    def ev_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    for name, sorted_ in [("colour_sorted", True), ("natural_order", False)]:
+        e = HpcgEll(NX, NY, NZ, levels=LEVELS, colour_sorted=sorted_, device=dev)
+        rows, slices, _ = e.level_info(0)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        solve_ms = ev_ms(lambda: e.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x), 2)
+        err = float((x - 1.0).abs().max())
+        xs = e.to_stored(b)
+        ys = torch.empty_like(xs)
+        sp_ms = ev_ms(lambda: e.spmv(xs, out=ys), 10)
+        # algorithmic bytes of one SpMV: every slot (8-byte value + 4-byte
+        # column, padding slots included) once, x once, y once
+        sp_bytes = slices * 27 * 32 * 12 + 16 * rows
+        zs = torch.zeros_like(xs)
+        sm_ms = ev_ms(lambda: e.rbgs(xs, zs), 5)
+        # one symmetric application: 16 colour phases, each reads the slots of
+        # its rows (all rows' slots when masked in natural order)
+        out[name] = {"ms_per_step": solve_ms, "max_abs_err_vs_ones": err,
+                     "max_abs_diff_x_vs_matrix_free": float((x - x_ref).abs().max()),
+                     "matrix_bytes": e.nbytes(), "spmv_ms": sp_ms, "spmv_bytes": sp_bytes,
+                     "spmv_gbs": sp_bytes / (sp_ms * 1e-3) / 1e9, "spmv_hbm_frac_of_measured": sp_bytes / (sp_ms * 1e-3) / 1e9 / peak,
+                     "smoother_ms": sm_ms, "hpcg_gflops": hpcg_flops_per_iter(NX, NY, NZ, LEVELS) * ITERS / (solve_ms * 1e-3) / 1e9}
+        del e, x, xs, ys, zs
+        torch.cuda.synchronize()
+    out["sorted_vs_natural_smoother_speedup"] = out["natural_order"]["smoother_ms"] / out["colour_sorted"]["smoother_ms"]
+    return out
+
+
 def hpcg_checks(prob, dev, stream):
     """The benchmark flow around the solver that HPCG runs (Section II-D): the
     symmetry test of A and of the preconditioner M, |x'Ay - y'Ax| and
@@ -521,6 +572,7 @@ def run_gpu(args):
         HpcgProblem(NX, NY, NZ, levels=LEVELS, precision="mixed", device=dev), b)}
     forms = {} if args.skip_forms else other_forms(dev, stream)
     checks = {} if args.skip_forms else hpcg_checks(prob, dev, stream)
+    ell = {} if args.skip_forms else ell_study(b, x, dev, stream)
 
     # --- end to end through the public API with host buffers
     b_h = b.cpu().pin_memory()
@@ -579,6 +631,7 @@ def run_gpu(args):
         "fp64_solve_variants": variants,
         "forms": forms,
         "hpcg_checks": checks,
+        "materialised_ell": ell,
         "e2e": e2e,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -300,6 +300,64 @@ int hpcg_persistent_levels(hpcg_handle h, int *first_level);
 #define HPCG_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const double *r_dev, double *z_dev, void *stream);
 
+/* --- materialised operator, rows grouped by colour (P^T A P) --------------------- */
+/* Section III-A: rows of one colour can be stored contiguously by permuting the
+ * system, P^T A P, so that each colour phase of the smoother reads a contiguous
+ * range.  This engine stores the 27-point operator of every level as a
+ * sliced-ELL matrix (FP64 values, int32 columns, 27 slots per row of which 8 to
+ * 27 are used, slices of 32 rows stored slot-major) and runs the SpMV, the
+ * colour phases, the injected residual, refinement, the V-cycle of Listing 1
+ * and PCG on it.  It exists beside the matrix-free kernels above to compare
+ * storage schemes; it has no kappa field, no mixed precision and no batches.
+ *
+ * Stored order: with colour_sorted = 1 the rows of colour k (color_i =
+ * (x&1) + 2(y&1) + 4(z&1), the greedy colouring) are the range
+ * [cstart[k], cstart[k+1]) and inside it in increasing natural index; with
+ * colour_sorted = 0 the stored order is the natural order and a colour phase
+ * tests the colour of every row.  Slots of a row hold its nonzeros in
+ * ascending natural column index; unused slots hold value 0 and the row's own
+ * column.  Vectors passed to the level calls below are in STORED order;
+ * hpcg_ell_permute converts.
+ *
+ * exact = 1: every product and sum is a separate IEEE operation (no fused
+ * multiply-add), sums start from 0.0 in slot order, and the colour update is
+ * (r_i - s_i + z_i d_i) / d_i with s_i including the diagonal (Listing 3), so
+ * the level calls reproduce a plain sequential CRS evaluation bit for bit;
+ * exact = 0 (faster) fuses the multiply-adds.
+ *
+ * Memory: hpcg_ell_setup allocates (cudaMalloc) about 12 * 27 bytes per row for
+ * the matrix plus vectors and maps, on the current device (2.5 GB at 192^3 with
+ * 4 levels); hpcg_ell_bytes reports the total.  Calls are ordered on `stream`;
+ * the handle serialises host threads.
+ * Errors: INVALID_ARG for null or aliased pointers, a level or colour out of
+ * range, and the grid rules of hpcg_setup; CUDA when an allocation or launch
+ * fails. */
+typedef struct hpcg_ell_ctx *hpcg_ell_handle;
+int hpcg_ell_setup(int nx, int ny, int nz, int levels, int colour_sorted, int exact, hpcg_ell_handle *out);
+int hpcg_ell_destroy(hpcg_ell_handle h);
+int hpcg_ell_bytes(hpcg_ell_handle h, size_t *bytes);
+/* info_host[0] = rows, [1] = slices of 32 rows, [2..10] = cstart[0..8] (all zero when not sorted). */
+int hpcg_ell_level_info(hpcg_ell_handle h, int level, long *info_host);
+/* perm_dev[p] (int32 [n], device) = natural row index of stored row p. */
+int hpcg_ell_permutation(hpcg_ell_handle h, int level, int *perm_dev, void *stream);
+/* Copies the slices: slot s of stored row p at ((p/32)*27 + s)*32 + p%32 of
+ * col_dev (int32) and val_dev (FP64), each of slices*27*32 entries. */
+int hpcg_ell_matrix(hpcg_ell_handle h, int level, int *col_dev, double *val_dev, void *stream);
+/* to_stored = 1: dst[p] = src[perm[p]]; 0: dst[perm[p]] = src[p] (FP64 [n], distinct buffers). */
+int hpcg_ell_permute(hpcg_ell_handle h, int level, int to_stored, const double *src_dev, double *dst_dev, void *stream);
+/* y = A x on `level` (stored order, x and y distinct). */
+int hpcg_ell_spmv(hpcg_ell_handle h, int level, const double *x_dev, double *y_dev, void *stream);
+/* One colour phase (Listings 2 and 3): rows of colour `color` updated in place in z. */
+int hpcg_ell_rbgs_color(hpcg_ell_handle h, int level, int color, const double *r_dev, double *z_dev, void *stream);
+/* One symmetric smoother application: colours 0..7, then 7..0, in place in z. */
+int hpcg_ell_rbgs(hpcg_ell_handle h, int level, const double *r_dev, double *z_dev, void *stream);
+/* z = M r on level 0 (Listing 1, stored order; z starts from 0 on every level). */
+int hpcg_ell_mg_vcycle(hpcg_ell_handle h, const double *r_dev, double *z_dev, void *stream);
+/* PCG as hpcg_pcg_solve (FP64, b and x in NATURAL order, x holds x0 on entry);
+ * the host reads the residual after every iteration when rel_tol > 0. */
+int hpcg_ell_pcg_solve(hpcg_ell_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol, hpcg_stats *stats,
+                       void *stream);
+
 /* --- diagnostics ------------------------------------------------------------------ */
 const char *hpcg_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (thread-unsafe). */

@@ -60,6 +60,18 @@ SIGNATURES = {
     "hpcg_profile_iteration": (_i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i, _vp]),
     "hpcg_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "hpcg_persistent_levels": (_i, [_vp, ctypes.POINTER(_i)]),
+    "hpcg_ell_setup": (_i, [_i, _i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "hpcg_ell_destroy": (_i, [_vp]),
+    "hpcg_ell_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "hpcg_ell_level_info": (_i, [_vp, _i, ctypes.POINTER(_l)]),
+    "hpcg_ell_permutation": (_i, [_vp, _i, _vp, _vp]),
+    "hpcg_ell_matrix": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_ell_permute": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "hpcg_ell_spmv": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_ell_rbgs_color": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "hpcg_ell_rbgs": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_ell_mg_vcycle": (_i, [_vp, _vp, _vp, _vp]),
+    "hpcg_ell_pcg_solve": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
     "hpcg_strerror": (ctypes.c_char_p, [_i]),
     "hpcg_last_cuda_error": (ctypes.c_char_p, []),
     "hpcg_launch_count": (_l, []),

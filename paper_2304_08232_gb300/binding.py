@@ -253,6 +253,115 @@ class HpcgProblem:
         return X, [_Stats(sts[k], hists[k]) for k in range(nrhs)]
 
 
+class HpcgEll:
+    """The operator stored as a sliced-ELL matrix with rows grouped by colour
+    (P^T A P, hpcg_ell_setup); colour_sorted=False keeps the natural order.
+    Level calls take vectors in the stored order (to_stored / to_natural)."""
+
+    def __init__(self, nx, ny, nz, levels=4, colour_sorted=True, exact=False, device=None):
+        self.lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("HpcgEll needs a CUDA device")
+        self.device = torch.device(device or "cuda")
+        self.dims, self.levels = (nx, ny, nz), levels
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.hpcg_ell_setup(nx, ny, nz, levels, 1 if colour_sorted else 0, 1 if exact else 0, ctypes.byref(h)),
+                  "hpcg_ell_setup")
+        self.h = h
+        self.n = nx * ny * nz
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.lib.hpcg_ell_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def nbytes(self):
+        v = ctypes.c_size_t()
+        check(self.lib.hpcg_ell_bytes(self.h, ctypes.byref(v)), "hpcg_ell_bytes")
+        return v.value
+
+    def level_info(self, level=0):
+        """(rows, slices, cstart[0..8])"""
+        buf = (ctypes.c_long * 11)()
+        check(self.lib.hpcg_ell_level_info(self.h, level, buf), "hpcg_ell_level_info")
+        return buf[0], buf[1], list(buf[2:11])
+
+    def permutation(self, level=0):
+        n = self.level_info(level)[0]
+        out = torch.empty(n, dtype=torch.int32, device=self.device)
+        check(self.lib.hpcg_ell_permutation(self.h, level, _ptr(out), _stream()), "hpcg_ell_permutation")
+        return out
+
+    def matrix(self, level=0):
+        """(col, val) of the slices, slot s of stored row p at ((p//32)*27 + s)*32 + p%32."""
+        slices = self.level_info(level)[1]
+        col = torch.empty(slices * 27 * 32, dtype=torch.int32, device=self.device)
+        val = torch.empty(slices * 27 * 32, dtype=_f64, device=self.device)
+        check(self.lib.hpcg_ell_matrix(self.h, level, _ptr(col), _ptr(val), _stream()), "hpcg_ell_matrix")
+        return col, val
+
+    def _n(self, level):
+        return self.level_info(level)[0]
+
+    def to_stored(self, v, level=0):
+        n = self._n(level)
+        _need(v, n, name="v")
+        out = torch.empty_like(v)
+        check(self.lib.hpcg_ell_permute(self.h, level, 1, _ptr(v), _ptr(out), _stream()), "hpcg_ell_permute")
+        return out
+
+    def to_natural(self, v, level=0):
+        n = self._n(level)
+        _need(v, n, name="v")
+        out = torch.empty_like(v)
+        check(self.lib.hpcg_ell_permute(self.h, level, 0, _ptr(v), _ptr(out), _stream()), "hpcg_ell_permute")
+        return out
+
+    def spmv(self, x, level=0, out=None):
+        n = self._n(level)
+        _need(x, n, name="x")
+        out = torch.empty_like(x) if out is None else _need(out, n, name="out")
+        check(self.lib.hpcg_ell_spmv(self.h, level, _ptr(x), _ptr(out), _stream()), "hpcg_ell_spmv")
+        return out
+
+    def rbgs_color(self, r, z, color, level=0):
+        n = self._n(level)
+        _need(r, n, name="r"), _need(z, n, name="z")
+        check(self.lib.hpcg_ell_rbgs_color(self.h, level, color, _ptr(r), _ptr(z), _stream()), "hpcg_ell_rbgs_color")
+        return z
+
+    def rbgs(self, r, z, level=0):
+        n = self._n(level)
+        _need(r, n, name="r"), _need(z, n, name="z")
+        check(self.lib.hpcg_ell_rbgs(self.h, level, _ptr(r), _ptr(z), _stream()), "hpcg_ell_rbgs")
+        return z
+
+    def mg_vcycle(self, r, out=None):
+        _need(r, self.n, name="r")
+        out = torch.empty_like(r) if out is None else _need(out, self.n, name="out")
+        check(self.lib.hpcg_ell_mg_vcycle(self.h, _ptr(r), _ptr(out), _stream()), "hpcg_ell_mg_vcycle")
+        return out
+
+    def pcg_solve(self, b, x0=None, max_iters=50, tol=0.0, out=None):
+        """b, x in natural order; returns (x, stats)."""
+        _need(b, self.n, name="b")
+        x = out if out is not None else (x0.clone() if x0 is not None else torch.zeros_like(b))
+        if out is not None:
+            if x0 is not None:
+                x.copy_(x0)
+            else:
+                x.zero_()
+        st, hist = _new_stats(max_iters)
+        rc = self.lib.hpcg_ell_pcg_solve(self.h, _ptr(b), _ptr(x), max_iters, tol, ctypes.byref(st), _stream())
+        check(rc, "hpcg_ell_pcg_solve", allow=(_lib.HPCG_ERR_NOT_CONVERGED,))
+        return x, _Stats(st, hist)
+
+
 class HpcgBatch:
     """A batch of independent grids (hpcg_setup_batch), vectors concatenated."""
 
