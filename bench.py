@@ -315,6 +315,23 @@ def ell_study(b, x_ref, dev, stream):
         del e, x, xs, ys, zs
         torch.cuda.synchronize()
     out["sorted_vs_natural_smoother_speedup"] = out["natural_order"]["smoother_ms"] / out["colour_sorted"]["smoother_ms"]
+    # the same solve with the grid split into two z-slabs (own rows, halo
+    # planes, colour-aware halo exchange), both slabs on this GPU
+    from paper_2304_08232_gb300 import HpcgSplit
+    sp = HpcgSplit(NX, NY, NZ, levels=LEVELS, device=dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    v0, k0 = sp.exchange_count()
+    sp.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x)
+    v1, k1 = sp.exchange_count()
+    solve_ms = ev_ms(lambda: sp.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x), 2)
+    halo0 = sp.info(0, 0)["halo"] + sp.info(0, 1)["halo"]
+    out["two_subdomains"] = {"ms_per_step": solve_ms, "max_abs_err_vs_ones": float((x - 1.0).abs().max()),
+                             "max_abs_diff_x_vs_matrix_free": float((x - x_ref).abs().max()),
+                             "halo_values_per_cg_iter": (v1 - v0) / ITERS, "exchange_steps_per_cg_iter": (k1 - k0) / ITERS,
+                             "finest_halo_values": halo0,
+                             "vs_colour_sorted_whole_grid": solve_ms / out["colour_sorted"]["ms_per_step"]}
+    del sp, x
+    torch.cuda.synchronize()
     return out
 
 

@@ -358,6 +358,45 @@ int hpcg_ell_mg_vcycle(hpcg_ell_handle h, const double *r_dev, double *z_dev, vo
 int hpcg_ell_pcg_solve(hpcg_ell_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol, hpcg_stats *stats,
                        void *stream);
 
+/* --- two sub-domains with colour-aware halo exchange ---------------------------- */
+/* The data distribution of the reference implementation (the paper's section on
+ * distributed execution) gives each node a box of the grid plus the boundary
+ * planes of its neighbours (halos), and the reference's smoother exchanges,
+ * after each colour, only the halo values of that colour.  This engine splits
+ * every level into the slabs z < nz/2 and z >= nz/2, each with its own rows
+ * (a sliced-ELL matrix grouped by colour, as hpcg_ell_*, whose columns index
+ * [own rows | halo rows]) and a copy of the neighbour's boundary plane, and runs
+ * the two slabs on one GPU one after the other on `stream`; an exchange is a
+ * device-to-device gather from the neighbour's vector.  Exchanges: after colour
+ * phase k the halo rows of colour k; after refinement colour 0 (the injected
+ * points); before an SpMV the whole halo.  The level calls give the same values
+ * as hpcg_ell_* on the whole grid (bit for bit with exact = 1); dot products sum
+ * per slab, then over the slabs.  Vectors are in NATURAL order.
+ *
+ * Grid rules: those of hpcg_setup, and nz divisible by 2^levels (each slab keeps
+ * at least one plane on the coarsest level).  hpcg_split_setup builds the maps
+ * on the host and allocates the matrices with cudaMalloc (about the size of
+ * hpcg_ell_setup's).
+ * Errors: INVALID_ARG for null or aliased pointers, a level or slab out of
+ * range, or the grid rules; CUDA when an allocation or launch fails. */
+typedef struct hpcg_split_ctx *hpcg_split_handle;
+int hpcg_split_setup(int nx, int ny, int nz, int levels, int exact, hpcg_split_handle *out);
+int hpcg_split_destroy(hpcg_split_handle h);
+/* info_host[0..1] = the slab's z range [z0, z1); [2] own rows; [3] halo rows;
+ * [4..12] own rows' colour starts; [13..21] halo rows' colour starts. */
+int hpcg_split_info(hpcg_split_handle h, int level, int domain, long *info_host);
+/* Halo values copied and exchange steps since setup (host counters). */
+int hpcg_split_exchange_count(hpcg_split_handle h, long *values_host, long *steps_host);
+/* y = A x on `level`. */
+int hpcg_split_spmv(hpcg_split_handle h, int level, const double *x_dev, double *y_dev, void *stream);
+/* One symmetric smoother application (colours 0..7, 7..0) from z, in place. */
+int hpcg_split_rbgs(hpcg_split_handle h, int level, const double *r_dev, double *z_dev, void *stream);
+/* z = M r (Listing 1). */
+int hpcg_split_mg_vcycle(hpcg_split_handle h, const double *r_dev, double *z_dev, void *stream);
+/* PCG as hpcg_pcg_solve (FP64; x holds x0 on entry). */
+int hpcg_split_pcg_solve(hpcg_split_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol,
+                         hpcg_stats *stats, void *stream);
+
 /* --- diagnostics ------------------------------------------------------------------ */
 const char *hpcg_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (thread-unsafe). */

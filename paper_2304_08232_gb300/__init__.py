@@ -7,5 +7,5 @@ torch tensors, streams from torch's current stream, and every step of the
 solve runs in the library's CUDA kernels.  There is no CPU fallback: without
 the built library, or without a GPU, the calls raise.
 """
-from .binding import (HpcgProblem, HpcgBatch, HpcgEll, HpcgSolve, hpcg_solve, launch_count)  # noqa: F401
+from .binding import (HpcgProblem, HpcgBatch, HpcgEll, HpcgSplit, HpcgSolve, hpcg_solve, launch_count)  # noqa: F401
 from ._lib import HpcgError, FP64, MIXED  # noqa: F401

@@ -72,6 +72,14 @@ SIGNATURES = {
     "hpcg_ell_rbgs": (_i, [_vp, _i, _vp, _vp, _vp]),
     "hpcg_ell_mg_vcycle": (_i, [_vp, _vp, _vp, _vp]),
     "hpcg_ell_pcg_solve": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
+    "hpcg_split_setup": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "hpcg_split_destroy": (_i, [_vp]),
+    "hpcg_split_info": (_i, [_vp, _i, _i, ctypes.POINTER(_l)]),
+    "hpcg_split_exchange_count": (_i, [_vp, ctypes.POINTER(_l), ctypes.POINTER(_l)]),
+    "hpcg_split_spmv": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_split_rbgs": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_split_mg_vcycle": (_i, [_vp, _vp, _vp, _vp]),
+    "hpcg_split_pcg_solve": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
     "hpcg_strerror": (ctypes.c_char_p, [_i]),
     "hpcg_last_cuda_error": (ctypes.c_char_p, []),
     "hpcg_launch_count": (_l, []),

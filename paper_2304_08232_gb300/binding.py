@@ -362,6 +362,78 @@ class HpcgEll:
         return x, _Stats(st, hist)
 
 
+class HpcgSplit:
+    """One grid as two z-slabs with their own rows and halos and colour-aware
+    halo exchange (hpcg_split_setup), run on one GPU; natural-order vectors."""
+
+    def __init__(self, nx, ny, nz, levels=4, exact=False, device=None):
+        self.lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("HpcgSplit needs a CUDA device")
+        self.device = torch.device(device or "cuda")
+        self.dims, self.levels = (nx, ny, nz), levels
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.hpcg_split_setup(nx, ny, nz, levels, 1 if exact else 0, ctypes.byref(h)), "hpcg_split_setup")
+        self.h = h
+        self.n = nx * ny * nz
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.lib.hpcg_split_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def info(self, level, domain):
+        """dict: z range, own rows, halo rows, colour starts of own and halo rows"""
+        b = (ctypes.c_long * 22)()
+        check(self.lib.hpcg_split_info(self.h, level, domain, b), "hpcg_split_info")
+        return {"z": (b[0], b[1]), "own": b[2], "halo": b[3], "cstart": list(b[4:13]), "hstart": list(b[13:22])}
+
+    def exchange_count(self):
+        v, s_ = ctypes.c_long(), ctypes.c_long()
+        check(self.lib.hpcg_split_exchange_count(self.h, ctypes.byref(v), ctypes.byref(s_)), "hpcg_split_exchange_count")
+        return v.value, s_.value
+
+    def _n(self, level):
+        return (self.dims[0] >> level) * (self.dims[1] >> level) * (self.dims[2] >> level)
+
+    def spmv(self, x, level=0, out=None):
+        n = self._n(level)
+        _need(x, n, name="x")
+        out = torch.empty_like(x) if out is None else _need(out, n, name="out")
+        check(self.lib.hpcg_split_spmv(self.h, level, _ptr(x), _ptr(out), _stream()), "hpcg_split_spmv")
+        return out
+
+    def rbgs(self, r, z, level=0):
+        n = self._n(level)
+        _need(r, n, name="r"), _need(z, n, name="z")
+        check(self.lib.hpcg_split_rbgs(self.h, level, _ptr(r), _ptr(z), _stream()), "hpcg_split_rbgs")
+        return z
+
+    def mg_vcycle(self, r, out=None):
+        _need(r, self.n, name="r")
+        out = torch.empty_like(r) if out is None else _need(out, self.n, name="out")
+        check(self.lib.hpcg_split_mg_vcycle(self.h, _ptr(r), _ptr(out), _stream()), "hpcg_split_mg_vcycle")
+        return out
+
+    def pcg_solve(self, b, x0=None, max_iters=50, tol=0.0, out=None):
+        _need(b, self.n, name="b")
+        x = out if out is not None else (x0.clone() if x0 is not None else torch.zeros_like(b))
+        if out is not None:
+            if x0 is not None:
+                x.copy_(x0)
+            else:
+                x.zero_()
+        st, hist = _new_stats(max_iters)
+        rc = self.lib.hpcg_split_pcg_solve(self.h, _ptr(b), _ptr(x), max_iters, tol, ctypes.byref(st), _stream())
+        check(rc, "hpcg_split_pcg_solve", allow=(_lib.HPCG_ERR_NOT_CONVERGED,))
+        return x, _Stats(st, hist)
+
+
 class HpcgBatch:
     """A batch of independent grids (hpcg_setup_batch), vectors concatenated."""
 

@@ -34,256 +34,9 @@
 
 #include "hpcg.h"
 #include "hpcg_ctx.h"
+#include "hpcg_ell.cuh"
 
-namespace {
-
-constexpr int kEllW = 27;             // slots per row
-constexpr int kSlice = 32;            // rows per slice
-constexpr int kEllThreads = 256;      // threads per block of the row kernels
-constexpr int kEllDotBlocks = 608;    // fixed grid of the dot products (4 per SM of 152), fixed summation order
-constexpr int kEllMaxLevels = 8;
-
-struct EllGeom {
-  int nx, ny, nz;
-  int sorted;       // 1: rows grouped by colour; 0: natural order
-  long n;
-  long cstart[9];   // sorted: rows of colour k at [cstart[k], cstart[k+1])
-};
-
-__host__ __device__ __forceinline__ int count_par(int n, int par) { return (n - par + 1) >> 1; }
-
-// stored index of grid point (x, y, z)
-__device__ __forceinline__ long ell_index(const EllGeom &g, int x, int y, int z) {
-  if (!g.sorted) return x + (long)g.nx * (y + (long)g.ny * z);
-  const int px = x & 1, py = y & 1, pz = z & 1;
-  const long cx = count_par(g.nx, px), cy = count_par(g.ny, py);
-  return g.cstart[px + 2 * py + 4 * pz] + (x >> 1) + cx * ((y >> 1) + cy * (long)(z >> 1));
-}
-
-// grid point of stored row p
-__device__ __forceinline__ void ell_coords(const EllGeom &g, long p, int &x, int &y, int &z) {
-  if (!g.sorted) {
-    x = (int)(p % g.nx);
-    y = (int)((p / g.nx) % g.ny);
-    z = (int)(p / ((long)g.nx * g.ny));
-    return;
-  }
-  int c = 0;
-  while (c < 7 && p >= g.cstart[c + 1]) ++c;
-  const int px = c & 1, py = (c >> 1) & 1, pz = c >> 2;
-  const long cx = count_par(g.nx, px), cy = count_par(g.ny, py);
-  const long k = p - g.cstart[c];
-  x = 2 * (int)(k % cx) + px;
-  y = 2 * (int)((k / cx) % cy) + py;
-  z = 2 * (int)(k / (cx * cy)) + pz;
-}
-
-// address of slot s of stored row p
-__device__ __forceinline__ long slot_of(long p, int s) { return ((p >> 5) * kEllW + s) * kSlice + (p & 31); }
-
-__device__ __forceinline__ long gtid() { return blockIdx.x * (long)blockDim.x + threadIdx.x; }
-
-// One thread per stored row (padding rows of the last slice included): the
-// row's slots, the diagonal and the natural index.
-__global__ void k_ell_build(EllGeom g, long nrows_padded, int *__restrict__ col, double *__restrict__ val, double *__restrict__ diag,
-                            int *__restrict__ perm) {
-  const long p = gtid();
-  if (p >= nrows_padded) return;
-  if (p >= g.n) {
-    for (int s = 0; s < kEllW; ++s) {
-      col[slot_of(p, s)] = 0;
-      val[slot_of(p, s)] = 0.0;
-    }
-    return;
-  }
-  int x, y, z;
-  ell_coords(g, p, x, y, z);
-  perm[p] = (int)(x + (long)g.nx * (y + (long)g.ny * z));
-  diag[p] = 26.0;
-  int s = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int zz = z + dz;
-    if (zz < 0 || zz >= g.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = y + dy;
-      if (yy < 0 || yy >= g.ny) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = x + dx;
-        if (xx < 0 || xx >= g.nx) continue;
-        const bool self = dx == 0 && dy == 0 && dz == 0;
-        col[slot_of(p, s)] = (int)ell_index(g, xx, yy, zz);
-        val[slot_of(p, s)] = self ? 26.0 : -1.0;
-        ++s;
-      }
-    }
-  }
-  for (; s < kEllW; ++s) {
-    col[slot_of(p, s)] = (int)p;
-    val[slot_of(p, s)] = 0.0;
-  }
-}
-
-// f2c[pc]: stored fine row of the fine point (2 xc, 2 yc, 2 zc) injected into
-// stored coarse row pc (Section II-E)
-__global__ void k_ell_f2c(EllGeom gf, EllGeom gc, int *__restrict__ f2c) {
-  const long pc = gtid();
-  if (pc >= gc.n) return;
-  int x, y, z;
-  ell_coords(gc, pc, x, y, z);
-  f2c[pc] = (int)ell_index(gf, 2 * x, 2 * y, 2 * z);
-}
-
-// sum over the slots of row p of val * v[col]
-template <bool EXACT>
-__device__ __forceinline__ double row_sum(long p, const int *__restrict__ col, const double *__restrict__ val, const double *__restrict__ v) {
-  const long base = ((p >> 5) * kEllW) * kSlice + (p & 31);
-  double s = 0.0;
-#pragma unroll
-  for (int k = 0; k < kEllW; ++k) {
-    const double a = __ldg(val + base + k * kSlice);
-    const double b = v[__ldg(col + base + k * kSlice)];
-    s = EXACT ? __dadd_rn(s, __dmul_rn(a, b)) : fma(a, b, s);
-  }
-  return s;
-}
-
-template <bool EXACT>
-__global__ void __launch_bounds__(kEllThreads) k_ell_spmv(long n, const int *__restrict__ col, const double *__restrict__ val,
-                                                          const double *__restrict__ x, double *__restrict__ y) {
-  const long p = gtid();
-  if (p < n) y[p] = row_sum<EXACT>(p, col, val, x);
-}
-
-// One colour phase (Listings 2 and 3) over stored rows [p0, p1): rows of
-// colour k (all of them when the rows are grouped; mask >= 0 tests the colour
-// of each row in natural order).  Rows of one colour have no neighbour of
-// their colour, so they update independently.
-template <bool EXACT>
-__global__ void __launch_bounds__(kEllThreads) k_ell_gs(long p0, long p1, int mask, EllGeom g, const int *__restrict__ col,
-                                                        const double *__restrict__ val, const double *__restrict__ diag,
-                                                        const double *__restrict__ r, double *__restrict__ z) {
-  const long p = p0 + gtid();
-  if (p >= p1) return;
-  if (mask >= 0) {
-    const int x = (int)(p % g.nx), y = (int)((p / g.nx) % g.ny), zz = (int)(p / ((long)g.nx * g.ny));
-    if ((x & 1) + 2 * (y & 1) + 4 * (zz & 1) != mask) return;
-  }
-  const double s = row_sum<EXACT>(p, col, val, z);
-  const double d = diag[p];
-  const double v = EXACT ? __dadd_rn(__dsub_rn(r[p], s), __dmul_rn(z[p], d)) : fma(z[p], d, r[p] - s);
-  z[p] = v / d;
-}
-
-// rc = injection of r - A z (Section II-E), only at the injected rows
-template <bool EXACT>
-__global__ void __launch_bounds__(kEllThreads) k_ell_restrict(long nc, const int *__restrict__ f2c, const int *__restrict__ col,
-                                                              const double *__restrict__ val, const double *__restrict__ r,
-                                                              const double *__restrict__ z, double *__restrict__ rc) {
-  const long pc = gtid();
-  if (pc >= nc) return;
-  const long pf = f2c[pc];
-  rc[pc] = EXACT ? __dsub_rn(r[pf], row_sum<true>(pf, col, val, z)) : r[pf] - row_sum<false>(pf, col, val, z);
-}
-
-// z[f2c] += zc (refinement, the transpose of injection)
-__global__ void __launch_bounds__(kEllThreads) k_ell_prolong(long nc, const int *__restrict__ f2c, const double *__restrict__ zc,
-                                                             double *__restrict__ z) {
-  const long pc = gtid();
-  if (pc >= nc) return;
-  const long pf = f2c[pc];
-  z[pf] = __dadd_rn(z[pf], zc[pc]);
-}
-
-__global__ void k_ell_fill(long n, double v, double *__restrict__ a) {
-  const long i = gtid();
-  if (i < n) a[i] = v;
-}
-
-// dst[p] = src[perm[p]] (natural -> stored) or dst[perm[p]] = src[p] (stored -> natural)
-__global__ void k_ell_permute(long n, int to_stored, const int *__restrict__ perm, const double *__restrict__ src, double *__restrict__ dst) {
-  const long p = gtid();
-  if (p >= n) return;
-  if (to_stored)
-    dst[p] = src[perm[p]];
-  else
-    dst[perm[p]] = src[p];
-}
-
-// ---------------------------------------------------------------------------
-// CG on the stored order: scalars stay on the device.
-struct EllCg {
-  double rtz, normr0, alpha, beta;
-};
-
-__device__ __forceinline__ double ell_block_sum(double v, double *sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-  __syncthreads();
-  return s;
-}
-
-// fixed-grid partial sums of a . b (one per block)
-__global__ void __launch_bounds__(kEllThreads) k_ell_dot(long n, const double *__restrict__ a, const double *__restrict__ b,
-                                                         double *__restrict__ part) {
-  __shared__ double sh[kEllThreads / 32];
-  double s = 0.0;
-  for (long i = gtid(); i < n; i += (long)gridDim.x * blockDim.x) s = fma(a[i], b[i], s);
-  s = ell_block_sum(s, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-enum EllScalar { ES_NORM0 = 0, ES_RTZ_FIRST, ES_RTZ, ES_PAP, ES_NORM };
-
-// one block: the partials in a fixed order, then the CG scalar of `kind`
-__global__ void __launch_bounds__(kEllThreads) k_ell_scalar(int kind, const double *__restrict__ part, EllCg *__restrict__ st,
-                                                            double *__restrict__ hist, int k) {
-  __shared__ double sh[kEllThreads / 32];
-  double v = 0.0;
-  for (int i = threadIdx.x; i < kEllDotBlocks; i += blockDim.x) v += part[i];
-  const double s = ell_block_sum(v, sh);
-  if (threadIdx.x != 0) return;
-  switch (kind) {
-    case ES_NORM0: st->normr0 = sqrt(s); break;
-    case ES_RTZ_FIRST: st->rtz = s; break;
-    case ES_RTZ: st->beta = s / st->rtz; st->rtz = s; break;
-    case ES_PAP: st->alpha = st->rtz / s; break;
-    default: hist[k] = sqrt(s) / st->normr0; break;
-  }
-}
-
-// w = a x + b y with host scalars
-__global__ void __launch_bounds__(kEllThreads) k_ell_axpby(long n, double a, const double *__restrict__ x, double b,
-                                                           const double *__restrict__ y, double *__restrict__ w) {
-  const long i = gtid();
-  if (i < n) w[i] = __dadd_rn(__dmul_rn(a, x[i]), __dmul_rn(b, y[i]));
-}
-
-// p = z (first iteration) or z + beta p
-__global__ void __launch_bounds__(kEllThreads) k_ell_update_p(long n, int first, const double *__restrict__ z, double *__restrict__ p,
-                                                              const EllCg *__restrict__ st) {
-  const long i = gtid();
-  if (i >= n) return;
-  p[i] = first ? z[i] : __dadd_rn(z[i], __dmul_rn(st->beta, p[i]));
-}
-
-// x += alpha p; r -= alpha Ap
-__global__ void __launch_bounds__(kEllThreads) k_ell_update_xr(long n, const double *__restrict__ p, const double *__restrict__ ap,
-                                                               double *__restrict__ x, double *__restrict__ r, const EllCg *__restrict__ st) {
-  const long i = gtid();
-  if (i >= n) return;
-  const double alpha = st->alpha;
-  x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
-  r[i] = __dsub_rn(r[i], __dmul_rn(alpha, ap[i]));
-}
-
-inline unsigned blocks_for(long n) { return (unsigned)((n + kEllThreads - 1) / kEllThreads); }
-
-}  // namespace
+using namespace hpcg_ell;
 
 // ---------------------------------------------------------------------------
 struct EllLevel {
@@ -439,7 +192,7 @@ static int ell_dot(hpcg_ell_ctx *h, const double *a, const double *b, int kind, 
   const long n = h->lv[0].g.n;
   k_ell_dot<<<kEllDotBlocks, kEllThreads, 0, s>>>(n, a, b, h->part);
   CKL("k_ell_dot");
-  k_ell_scalar<<<1, kEllThreads, 0, s>>>(kind, h->part, h->st, h->hist, k);
+  k_ell_scalar<<<1, kEllThreads, 0, s>>>(kind, h->part, kEllDotBlocks, h->st, h->hist, k);
   CKL("k_ell_scalar");
   return HPCG_OK;
 }
