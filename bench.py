@@ -305,13 +305,18 @@ def ell_study(b, x_ref, dev, stream):
         sp_bytes = slices * 27 * 32 * 12 + 16 * rows
         zs = torch.zeros_like(xs)
         sm_ms = ev_ms(lambda: e.rbgs(xs, zs), 5)
-        # one symmetric application: 16 colour phases, each reads the slots of
-        # its rows (all rows' slots when masked in natural order)
+        # one symmetric application: 16 colour phases; algorithmic bytes of a
+        # phase: the slots of its eighth of the rows, r and z of those rows
+        # (z read and written), and the z of the other seven colours its rows
+        # neighbour, once (the same count for both layouts: a masked phase in
+        # natural order drags in slots of rows of other colours as well)
+        sm_bytes = 16 * (slices * 27 * 32 * 12 / 8 + 8 * 3 * rows / 8 + 8 * 7 * rows / 8)
         out[name] = {"ms_per_step": solve_ms, "max_abs_err_vs_ones": err,
                      "max_abs_diff_x_vs_matrix_free": float((x - x_ref).abs().max()),
                      "matrix_bytes": e.nbytes(), "spmv_ms": sp_ms, "spmv_bytes": sp_bytes,
                      "spmv_gbs": sp_bytes / (sp_ms * 1e-3) / 1e9, "spmv_hbm_frac_of_measured": sp_bytes / (sp_ms * 1e-3) / 1e9 / peak,
-                     "smoother_ms": sm_ms, "hpcg_gflops": hpcg_flops_per_iter(NX, NY, NZ, LEVELS) * ITERS / (solve_ms * 1e-3) / 1e9}
+                     "smoother_ms": sm_ms, "smoother_bytes": sm_bytes,
+                     "smoother_hbm_frac_of_measured": sm_bytes / (sm_ms * 1e-3) / 1e9 / peak, "hpcg_gflops": hpcg_flops_per_iter(NX, NY, NZ, LEVELS) * ITERS / (solve_ms * 1e-3) / 1e9}
         del e, x, xs, ys, zs
         torch.cuda.synchronize()
     out["sorted_vs_natural_smoother_speedup"] = out["natural_order"]["smoother_ms"] / out["colour_sorted"]["smoother_ms"]
@@ -672,6 +677,9 @@ def main():
     ap.add_argument("--shapes", default=None,
                     help="JSON list of per-level launch shapes [[row lines, row planes, line lines, line planes], ...] "
                          "to use instead of autotuning (repeatable profiling runs)")
+    ap.add_argument("--ell-only", action="store_true",
+                    help="run only the materialised-operator study (sliced-ELL, colour-sorted and natural order, two "
+                         "sub-domains) at the grid size and print its JSON (profiling runs)")
     ap.add_argument("--quick", action="store_true",
                     help="time the FP64 solve only (no kernel roofline, mixed comparison, e2e or CPU baseline)")
     args = ap.parse_args()
@@ -681,7 +689,22 @@ def main():
         NX, NY, NZ = (int(v) for v in args.dims.split(","))
     if args.impl == "reference":
         return run_reference(args)
+    if args.ell_only:
+        return run_ell_only()
     return run_gpu(args)
+
+
+def run_ell_only():
+    import torch
+    from paper_2304_08232_gb300 import HpcgProblem
+    dev = torch.device("cuda", 0)
+    prob = HpcgProblem(NX, NY, NZ, levels=LEVELS, device=dev)
+    b = prob.get_rhs()
+    x = torch.zeros_like(b)
+    prob.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x)
+    torch.cuda.synchronize()
+    print(json.dumps({"grid": [NX, NY, NZ], "materialised_ell": ell_study(b, x, dev, torch.cuda.current_stream())}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
