@@ -52,6 +52,36 @@ def hpcg_flops_per_iter(nx, ny, nz, levels):
     return f
 
 
+def algorithmic_bytes_per_iter(nx, ny, nz, levels, precision="fp64", kappa=False):
+    """Bytes one CG iteration must move at least, per row of each level, with
+    every vector touched once per pass (FP64 unless noted):
+      finest level: SpMV 16 (x read, y written; + 8 for kappa), CG vector
+        passes 88 (x, p, r, Ap -> x, r: 48; r, z, p -> p with r.z: 40);
+      each level but the coarsest: two symmetric smoother applications of 48
+        (r once, z read and written once per sweep direction), the residual
+        with restriction 9, refinement 2; the coarsest level one application.
+    precision "mixed": the preconditioner's vectors are FP32 (24, 4.5 and 1;
+    + 4 per application with kappa for the FP32 inverse diagonal) and the CG
+    passes read the FP32 z and write an FP32 copy of r (84)."""
+    sz = level_sizes(nx, ny, nz, levels)
+    n0 = sz[0][0]
+    f = 4 if precision == "mixed" else 8
+    sweep = 6 * f + (4 if (kappa and precision == "mixed") else (8 if kappa else 0))
+    b = (16 + (8 if kappa else 0)) * n0 + (84 if precision == "mixed" else 88) * n0
+    for l in range(levels):
+        n = sz[l][0]
+        if l < levels - 1:
+            b += 2 * sweep * n + (9 * f / 8) * n + (2 * f / 8) * n
+        else:
+            b += sweep * n
+    return b
+
+
+def whole_solve_roofline(bytes_total, ms, peak):
+    gbs = bytes_total / (ms * 1e-3) / 1e9
+    return {"bytes": bytes_total, "ms": ms, "gbs": gbs, "frac": gbs / peak}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -234,8 +264,11 @@ def other_forms(dev, stream):
     ms, (X, sts) = timed(lambda: g.pcg_solve_multi(B, max_iters=1000, tol=1e-8))
     its = [s_.iters for s_ in sts]
     fl = hpcg_flops_per_iter(128, 128, 128, 4) * sum(its)
+    peak = measured_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS)
     res["multi_rhs_32x128^3"] = {"ms": ms, "iters_max": max(its), "iters_sum": sum(its),
-                                 "converged": all(s_.converged for s_ in sts), "hpcg_gflops": fl / (ms * 1e-3) / 1e9}
+                                 "converged": all(s_.converged for s_ in sts), "hpcg_gflops": fl / (ms * 1e-3) / 1e9,
+                                 "whole_solve_roofline": whole_solve_roofline(
+                                     algorithmic_bytes_per_iter(128, 128, 128, 4) * sum(its), ms, peak)}
     del g, B, X
     # (b) 64 grids with edges from {32,48,64,80,96} (seed 3), 4 levels, to 1e-8
     dims = [tuple(int(v) for v in d) for d in uneven_batch_dims(64, seed=3)]
@@ -243,8 +276,10 @@ def other_forms(dev, stream):
     bb = torch.as_tensor(normal(bat.n, 3), device=dev)
     ms, (xb, sts) = timed(lambda: bat.pcg_solve(bb, max_iters=1000, tol=1e-8))
     fl = sum(hpcg_flops_per_iter(*d, 4) * s_.iters for d, s_ in zip(dims, sts))
+    by = sum(algorithmic_bytes_per_iter(*d, 4) * s_.iters for d, s_ in zip(dims, sts))
     res["batch_64_uneven_grids"] = {"ms": ms, "rows": bat.n, "iters_max": max(s_.iters for s_ in sts),
-                                    "converged": all(s_.converged for s_ in sts), "hpcg_gflops": fl / (ms * 1e-3) / 1e9}
+                                    "converged": all(s_.converged for s_ in sts), "hpcg_gflops": fl / (ms * 1e-3) / 1e9,
+                                    "whole_solve_roofline": whole_solve_roofline(by, ms, peak)}
     del bat, bb, xb
     # (c) differentiable solve at 96^3: forward + adjoint backward, FP64 outer, FP32 M
     n = 96 ** 3
@@ -263,7 +298,12 @@ def other_forms(dev, stream):
         return loss
 
     ms, loss = timed(fwd_bwd)
-    res["differentiable_96^3"] = {"ms_forward_backward": ms, "loss": float(loss), "tol": 1e-10}
+    itf, itb = g.last_forward_stats.iters, g.last_backward_stats.iters
+    # forward and adjoint solves (mixed, kappa), + the gradient pass (lambda, x read, grad written)
+    by = algorithmic_bytes_per_iter(96, 96, 96, 4, "mixed", kappa=True) * (itf + itb) + 24 * n
+    res["differentiable_96^3"] = {"ms_forward_backward": ms, "loss": float(loss), "tol": 1e-10,
+                                  "iters_forward": itf, "iters_backward": itb,
+                                  "whole_solve_roofline": whole_solve_roofline(by, ms, peak)}
     return res
 
 
@@ -594,6 +634,30 @@ def run_gpu(args):
         HpcgProblem(NX, NY, NZ, levels=LEVELS, precision="mixed", device=dev), b)}
     forms = {} if args.skip_forms else other_forms(dev, stream)
     checks = {} if args.skip_forms else hpcg_checks(prob, dev, stream)
+    # --- every form against the HBM roofline: the dominant kernel where one
+    # kernel dominates (single-grid forms), and the whole solve against the
+    # per-row byte model of algorithmic_bytes_per_iter
+    mixed_l0_ms = breakdown["mixed"]["smoother_ms"][0]
+    mixed_l0_bytes = 74.5 * n  # FP32 analogue of the 158 n above: runs of 2, 3, 4, 5, 6, 6, 6 n (+ 0.5 n restricted
+    #                            residual) before the coarse correction, 7 x 6 n after it (refinement is its own kernel)
+    by_form = {
+        "fp64_192^3_50_iters": {
+            "dominant_kernel": roofline["kernel"], "dominant_kernel_frac": roofline["frac"],
+            "whole_solve_roofline": whole_solve_roofline(algorithmic_bytes_per_iter(NX, NY, NZ, LEVELS) * ITERS, ms, hbm_peak)},
+        "mixed_192^3_to_1e-9": {
+            "dominant_kernel": "k_gs_lines<float,3,PAIR> (finest level, FP32 colour-pair runs)",
+            "dominant_kernel_bytes_per_vcycle": mixed_l0_bytes, "dominant_kernel_ms_per_vcycle": mixed_l0_ms,
+            "dominant_kernel_frac": mixed_l0_bytes / (mixed_l0_ms * 1e-3) / 1e9 / hbm_peak,
+            "whole_solve_roofline": whole_solve_roofline(
+                algorithmic_bytes_per_iter(NX, NY, NZ, LEVELS, "mixed") * mixed_vs["mixed"]["iters"], mixed_vs["mixed"]["ms"],
+                hbm_peak)},
+    }
+    for k, v in forms.items():
+        if "whole_solve_roofline" in v:
+            by_form[k] = {"whole_solve_roofline": v["whole_solve_roofline"]}
+    by_form["byte_model"] = ("whole solve: per CG iteration, finest SpMV 16 B/row (+8 kappa) + CG passes 88 (84 mixed); per "
+                             "non-coarsest level 2 x 48 (symmetric smoother) + 9 (residual, restriction) + 2 (refinement), "
+                             "coarsest 48; FP32 preconditioner halves its terms; = 226 B/row at 192^3 FP64")
     ell = {} if args.skip_forms else ell_study(b, x, dev, stream)
 
     # --- end to end through the public API with host buffers
@@ -648,6 +712,7 @@ def run_gpu(args):
         "roofline": roofline,
         "hbm_peak": {"value": peaks.get("hbm_gbs"), "kind": peak_kind},
         "mixed_vs_fp64_to_1e-9": mixed_vs,
+        "roofline_by_form": by_form,
         "spmv": spmv,
         "iteration_breakdown": breakdown,
         "fp64_solve_variants": variants,

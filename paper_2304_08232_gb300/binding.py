@@ -493,13 +493,15 @@ class HpcgSolve(torch.autograd.Function):
         ctx.problem, ctx.max_iters, ctx.tol = problem, max_iters, tol
         ctx.save_for_backward(x)
         ctx.forward_stats = st
+        problem.last_forward_stats = st
         return x
 
     @staticmethod
     def backward(ctx, grad_x):
         (x,) = ctx.saved_tensors
-        gb, gk, _ = ctx.problem.pcg_backward(x, grad_x.contiguous(), max_iters=ctx.max_iters, tol=ctx.tol,
-                                             want_kappa=ctx.needs_input_grad[1])
+        gb, gk, st = ctx.problem.pcg_backward(x, grad_x.contiguous(), max_iters=ctx.max_iters, tol=ctx.tol,
+                                              want_kappa=ctx.needs_input_grad[1])
+        ctx.problem.last_backward_stats = st
         return gb, gk, None, None, None
 
 

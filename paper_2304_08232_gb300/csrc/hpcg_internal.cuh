@@ -21,7 +21,7 @@ constexpr int kBlock = kTileX * kTileY;
 constexpr int kRedThreads = 256; // threads of a reduction block
 constexpr int kFinThreads = 1024; // threads of a finalize block (one per instance)
 constexpr int kRedItems = 8;     // elements per thread per reduction block (before the block strides)
-constexpr int kMaxRedBlocksPerInst = 592;  // 4 x 148... fixed cap keeps reductions deterministic
+constexpr int kMaxRedBlocksPerInst = 2432;  // 16 per SM of 152; a fixed cap keeps reductions deterministic
 constexpr int kHistoryCap = 8192;
 constexpr int kRawDotBlocks = 304;  // fixed grid of the plain dot product (2 x 152 SMs)
 
