@@ -1028,9 +1028,11 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   }
   prof_mark(PK_FINALIZE, 0);
   if (mixed)
-    launch_k(k_update_p<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const float *)L0.z32, h->cg_p, h->st);
+    launch_k(k_update_p<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const float *)L0.z32, h->cg_p,
+             (double *)nullptr, h->st);
   else
-    launch_k(k_update_p<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_z, h->cg_p, h->st);
+    launch_k(k_update_p<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_z, h->cg_p, x,
+             h->st);  // with the previous iteration's x += alpha p (FP64: x is read only at restarts, which FP64 has not)
   CKL("k_update_p");
   prof_mark(PK_UPDATE, 0);
   TRY((enqueue_spmv<double, 0>(h, 0, h->cg_p, nullptr, h->cg_ap, kap, h->part, h->st, s)));  // Ap, p.Ap partials
@@ -1042,7 +1044,7 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
     CKL("k_finalize<PAP>");
   }
   prof_mark(PK_FINALIZE, 0);
-  launch_k(k_update_xr, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_p, h->cg_ap, x, h->cg_r,
+  launch_k(k_update_xr, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_p, h->cg_ap, mixed ? x : nullptr, h->cg_r,
            mixed ? L0.r32 : nullptr, h->part, h->st);
   CKL("k_update_xr");
   prof_mark(PK_UPDATE, 0);
@@ -1092,6 +1094,17 @@ static int get_iter_graph(hpcg_ctx *h, const double *b, double *x, cudaGraphExec
   g.kernels = nk;
   *out = g.exec;
   *kernels = nk;
+  return HPCG_OK;
+}
+
+// The last x += alpha p of every instance: the FP64 iterations defer it to the
+// next iteration's p update, so a solve ends with it.
+static int enqueue_x_pending(hpcg_ctx *h, double *x, cudaStream_t s) {
+  if (h->opt.precision == HPCG_MIXED) return HPCG_OK;
+  const LevelData &L0 = h->lv[0];
+  launch_k(k_update_x_pending, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_p, x,
+           (const CgState *)h->st);
+  CKL("k_update_x_pending");
   return HPCG_OK;
 }
 
@@ -1146,6 +1159,7 @@ static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, doubl
       }
     }
   }
+  if (rc == HPCG_OK) rc = enqueue_x_pending(h, x, s);
   if (rc == HPCG_OK) {
     cudaError_t e = cudaMemcpyAsync(hs.data(), h->st, sizeof(CgState) * h->count, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1308,6 +1322,7 @@ int hpcg_profile_iteration(hpcg_handle h, const double *b_dev, double *x_dev, do
   prof_mark(PK_COUNT, 0);  // start
   int rc = enqueue_pcg_iter(h, b_dev, x_dev, s);
   t_prof = nullptr;
+  if (rc == HPCG_OK) rc = enqueue_x_pending(h, x_dev, s);
   cudaError_t e = cudaStreamSynchronize(s);
   for (int i = 0; i < 3 * L + 7; ++i) ms_host[i] = 0.0;
   if (rc == HPCG_OK && e == cudaSuccess) {

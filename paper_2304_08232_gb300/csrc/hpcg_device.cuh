@@ -93,7 +93,7 @@ enum FinKind { FIN_NORM0 = 0, FIN_RTZ = 1, FIN_PAP = 2, FIN_NORM = 3, FIN_OUT = 
 // CG scalar update of one instance from a finished reduction s (thread 0 only):
 //  FIN_NORM0: normr0 = sqrt(s)            (start of the solve)
 //  FIN_RTZ:   rtz' = s; beta = rtz'/rtz   (after z = M r)
-//  FIN_PAP:   alpha = rtz / s             (after Ap = A p; breakdown check)
+//  FIN_PAP:   alpha = rtz / s             (after Ap = A p; breakdown check; x += alpha p pending)
 //  FIN_NORM:  normr = sqrt(s); history; convergence and stall tests
 // hist points at this instance's history row (nullable).
 template <int Kind>
@@ -129,8 +129,10 @@ __device__ __forceinline__ void fin_apply(CgState &c, double s, double *hist) {
       c.done = 1;
       c.status = HPCG_ERR_BREAKDOWN;
       c.alpha = 0.0;
+      c.xpend = 0;
     } else {
       c.alpha = c.rtz / s;
+      c.xpend = 1;
     }
     c.first = 0;
   } else if (Kind == FIN_NORM) {

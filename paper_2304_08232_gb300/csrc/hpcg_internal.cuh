@@ -68,7 +68,9 @@ struct CgState {
   double rtz, pAp, alpha, beta, normr, normr0, best, tol;
   double hist_prev[3];
   int iter, done, status, first, restart, restarts, stall, max_iters;
-  int converged, mixed, pad0, pad1;
+  int converged, mixed;
+  int xpend;  // x += alpha p of this alpha is still to be applied (the FP64 solve defers it to the next p update)
+  int pad1;
 };
 
 // Blocks of a 32x8-tiled launch over an nx x ny x nz box, one z-plane per tile row.

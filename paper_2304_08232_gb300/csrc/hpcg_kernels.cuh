@@ -292,10 +292,13 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize_lines(const Inst *__re
 }
 
 // p = z + beta p (p = z on the first iteration or after a restart); z in FP64
-// or the FP32 preconditioner output (widened exactly)
+// or the FP32 preconditioner output (widened exactly).  x (nullable): the
+// previous iteration's x += alpha p, deferred to this pass (it reads the same
+// old p), when that update is pending.
 template <typename TZ>
 __global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict__ tab, int count, const TZ *__restrict__ zv,
-                                                          double *__restrict__ p, const CgState *__restrict__ st) {
+                                                          double *__restrict__ p, double *__restrict__ x,
+                                                          const CgState *__restrict__ st) {
   pdl_enter();
   const int blk = blockIdx.x;
   const int ii = find_inst<2>(tab, count, blk);
@@ -304,16 +307,43 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict
   if (c.done) return;
   const bool first = c.first;
   const double beta = c.beta;
+  const double alpha = c.alpha;
+  const bool upd_x = x && c.xpend;
   const long stride = (long)g.nred * kRedThreads;
   #pragma unroll 4
   for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
     const long gi = g.off + i;
     const double zi = (double)zv[gi];
-    p[gi] = first ? zi : zi + beta * p[gi];
+    if (upd_x) {
+      const double po = p[gi];
+      x[gi] = x[gi] + alpha * po;
+      p[gi] = zi + beta * po;
+    } else {
+      p[gi] = first ? zi : zi + beta * p[gi];
+    }
   }
 }
 
-// x += alpha p; r -= alpha Ap; partials of r.r
+// x += alpha p for every instance whose last update is still pending (end of a
+// solve whose x updates were deferred)
+__global__ void __launch_bounds__(kRedThreads) k_update_x_pending(const Inst *__restrict__ tab, int count, const double *__restrict__ p,
+                                                                  double *__restrict__ x, const CgState *__restrict__ st) {
+  pdl_enter();
+  const int blk = blockIdx.x;
+  const int ii = find_inst<2>(tab, count, blk);
+  const Inst g = tab[ii];
+  const CgState &c = st[ii];
+  if (!c.xpend) return;
+  const double alpha = c.alpha;
+  const long stride = (long)g.nred * kRedThreads;
+  #pragma unroll 4
+  for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
+    const long gi = g.off + i;
+    x[gi] = x[gi] + alpha * p[gi];
+  }
+}
+
+// x += alpha p (x nullable: deferred to the next p update); r -= alpha Ap; partials of r.r
 __global__ void __launch_bounds__(kRedThreads) k_update_xr(const Inst *__restrict__ tab, int count, const double *__restrict__ p,
                                                            const double *__restrict__ ap, double *__restrict__ x,
                                                            double *__restrict__ r, float *__restrict__ r32, double *__restrict__ partials,
@@ -331,7 +361,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(const Inst *__restric
     #pragma unroll 4
     for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
       const long gi = g.off + i;
-      x[gi] = x[gi] + alpha * p[gi];
+      if (x) x[gi] = x[gi] + alpha * p[gi];
       const double rn = r[gi] - alpha * ap[gi];
       r[gi] = rn;
       if (r32) r32[gi] = (float)rn;  // the FP32 preconditioner's copy (mixed precision)
