@@ -90,6 +90,9 @@ typedef struct {
                        by the cluster barrier instead of kernel boundaries (same bits as one launch
                        per run); 0 (default): one launch per run on every level, which measured
                        faster on one 192^3 grid (16 SMs do the coarse runs slower than launches) */
+  int restart_every; /* mixed precision: also replace the recurrence residual by b - A x (FP64) after
+                        every this many iterations, besides the stall rule (no 1% progress in 3
+                        iterations); 0 (default): on stalls only */
 } hpcg_options;
 
 typedef struct {

@@ -977,6 +977,7 @@ static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_ite
     c.tol = tol;
     c.max_iters = max_iters;
     c.mixed = h->opt.precision == HPCG_MIXED;
+    c.restart_every = c.mixed && h->opt.restart_every > 0 ? h->opt.restart_every : 0;
     c.status = HPCG_OK;
   }
   CK(cudaMemcpyAsync(h->st, init.data(), sizeof(CgState) * h->count, cudaMemcpyHostToDevice, s));
@@ -1003,6 +1004,9 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   const double *kap = h->has_kappa ? L0.kap : nullptr;
   const bool mixed = h->opt.precision == HPCG_MIXED;
   if (mixed) {
+    launch_k(k_update_x_restart, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_p, x,
+             (const CgState *)h->st);
+    CKL("k_update_x_restart");
     launch_k(k_restart_residual, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, x, b, h->cg_r, L0.r32, kap, h->st);
     CKL("k_restart_residual");
     prof_mark(PK_UPDATE, 0);
@@ -1028,11 +1032,10 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
   }
   prof_mark(PK_FINALIZE, 0);
   if (mixed)
-    launch_k(k_update_p<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const float *)L0.z32, h->cg_p,
-             (double *)nullptr, h->st);
+    launch_k(k_update_p<float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const float *)L0.z32, h->cg_p, x, h->st);
   else
     launch_k(k_update_p<double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_z, h->cg_p, x,
-             h->st);  // with the previous iteration's x += alpha p (FP64: x is read only at restarts, which FP64 has not)
+             h->st);  // with the previous iteration's x += alpha p
   CKL("k_update_p");
   prof_mark(PK_UPDATE, 0);
   TRY((enqueue_spmv<double, 0>(h, 0, h->cg_p, nullptr, h->cg_ap, kap, h->part, h->st, s)));  // Ap, p.Ap partials
@@ -1044,7 +1047,7 @@ static int enqueue_pcg_iter(hpcg_ctx *h, const double *b, double *x, cudaStream_
     CKL("k_finalize<PAP>");
   }
   prof_mark(PK_FINALIZE, 0);
-  launch_k(k_update_xr, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_p, h->cg_ap, mixed ? x : nullptr, h->cg_r,
+  launch_k(k_update_xr, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, h->cg_p, h->cg_ap, (double *)nullptr, h->cg_r,
            mixed ? L0.r32 : nullptr, h->part, h->st);
   CKL("k_update_xr");
   prof_mark(PK_UPDATE, 0);
@@ -1097,10 +1100,9 @@ static int get_iter_graph(hpcg_ctx *h, const double *b, double *x, cudaGraphExec
   return HPCG_OK;
 }
 
-// The last x += alpha p of every instance: the FP64 iterations defer it to the
-// next iteration's p update, so a solve ends with it.
+// The last x += alpha p of every instance: the iterations defer it to the next
+// iteration's p update, so a solve ends with it.
 static int enqueue_x_pending(hpcg_ctx *h, double *x, cudaStream_t s) {
-  if (h->opt.precision == HPCG_MIXED) return HPCG_OK;
   const LevelData &L0 = h->lv[0];
   launch_k(k_update_x_pending, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, (const double *)h->cg_p, x,
            (const CgState *)h->st);
@@ -1438,6 +1440,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->persistent = 0;
   opt->block_fp = 1;
   opt->cluster_tail = 0;
+  opt->restart_every = 0;
   return HPCG_OK;
 }
 

@@ -159,6 +159,7 @@ __device__ __forceinline__ void fin_apply(CgState &c, double s, double *hist) {
         c.stall = 0;
         c.best = c.normr;
       }
+      if (c.restart_every > 0 && c.iter % c.restart_every == 0) c.restart = 1;  // periodic replacement
     }
   }
 }

@@ -69,8 +69,8 @@ struct CgState {
   double hist_prev[3];
   int iter, done, status, first, restart, restarts, stall, max_iters;
   int converged, mixed;
-  int xpend;  // x += alpha p of this alpha is still to be applied (the FP64 solve defers it to the next p update)
-  int pad1;
+  int xpend;  // x += alpha p of this alpha is still to be applied (deferred to the next p update)
+  int restart_every;  // mixed precision: residual replacement every this many iterations (0: on stalls only)
 };
 
 // Blocks of a 32x8-tiled launch over an nx x ny x nz box, one z-plane per tile row.

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict
   const bool first = c.first;
   const double beta = c.beta;
   const double alpha = c.alpha;
-  const bool upd_x = x && c.xpend;
+  const bool upd_x = x && c.xpend && !first;  // after a restart the pending update was applied before it
   const long stride = (long)g.nred * kRedThreads;
   #pragma unroll 4
   for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
@@ -321,6 +321,25 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict
     } else {
       p[gi] = first ? zi : zi + beta * p[gi];
     }
+  }
+}
+
+// Mixed precision: an instance that restarts this iteration (r = b - A x)
+// needs x current, so its pending x += alpha p is applied first.
+__global__ void __launch_bounds__(kRedThreads) k_update_x_restart(const Inst *__restrict__ tab, int count, const double *__restrict__ p,
+                                                                  double *__restrict__ x, const CgState *__restrict__ st) {
+  pdl_enter();
+  const int blk = blockIdx.x;
+  const int ii = find_inst<2>(tab, count, blk);
+  const Inst g = tab[ii];
+  const CgState &c = st[ii];
+  if (c.done || !c.restart || !c.xpend) return;
+  const double alpha = c.alpha;
+  const long stride = (long)g.nred * kRedThreads;
+  #pragma unroll 4
+  for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
+    const long gi = g.off + i;
+    x[gi] = x[gi] + alpha * p[gi];
   }
 }
 

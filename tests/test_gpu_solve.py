@@ -75,6 +75,32 @@ def test_mixed_precision_vcycle_and_solve():
     assert np.linalg.norm(b - o.spmv(host(x))) / np.linalg.norm(b) <= 2e-9
 
 
+@pytest.mark.parametrize("dims,every", [((32, 32, 32), 5), ((48, 32, 64), 3), ((32, 32, 32), 1)])
+def test_mixed_precision_restarts_keep_x_consistent(dims, every):
+    """Residual replacement r = b - A x every few iterations (besides the stall
+    rule, which MG-preconditioned CG rarely meets): x carries every deferred
+    update into each replacement exactly once, so the true residual, recomputed
+    by the oracle, stays with the recurrence, and x matches the FP64 solve."""
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    n = int(np.prod(dims))
+    o = OracleProblem(*dims, levels=4)
+    b = o.spmv(mixed_precision_xtrue(n, seed=6))
+    g = HpcgProblem(*dims, levels=4, precision="mixed", restart_every=every)
+    x, st = g.pcg_solve(dev(b), max_iters=300, tol=1e-12)
+    assert st.converged and st.restarts >= st.iters // every - 1 >= 1
+    true_rel = np.linalg.norm(b - o.spmv(host(x))) / np.linalg.norm(b)
+    # x0 = 0, so the recurrence residual is relative to ||b||; an update applied
+    # twice or lost across a replacement would leave r and x inconsistent
+    assert true_rel <= 10 * st.rel_res + 1e-14
+    xf, _ = HpcgProblem(*dims, levels=4).pcg_solve(dev(b), max_iters=300, tol=1e-13)
+    assert normwise(host(x), host(xf)) <= 1e-9
+    _, s0 = HpcgProblem(*dims, levels=4, precision="mixed").pcg_solve(dev(b), max_iters=300, tol=1e-12)
+    # each replacement also restarts the CG direction (p = z), so convergence
+    # slows but stays MG-driven (every iteration: preconditioned steepest descent)
+    assert s0.restarts == 0 and s0.iters <= st.iters <= 6 * s0.iters
+
+
 def test_differentiable_solve_gradients():
     from paper_2304_08232_gb300 import HpcgProblem, hpcg_solve
     need_gpu()
