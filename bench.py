@@ -381,7 +381,7 @@ def ell_study(b, x_ref, dev, stream):
 
 
 def hpcg_checks(prob, dev, stream):
-    """The benchmark flow around the solver that HPCG runs (Section II-D): the
+    """The benchmark flow around the solver that HPCG runs (Sections II-A, III-A): the
     symmetry test of A and of the preconditioner M, |x'Ay - y'Ax| and
     |x'My - y'Mx| for random x, y in units of eps ||x|| ||y|| ||A||_inf
     (||A||_inf = 52; for M the bound 1/26 of a Jacobi step stands in), and a

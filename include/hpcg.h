@@ -22,7 +22,7 @@
  *  - Colour classes (Section III-A, greedy colouring, eight colours on this
  *    grid) are color_i = (x&1) + 2(y&1) + 4(z&1); coarse level l+1 has each
  *    dimension halved and coarse row c = (xc,yc,zc) is injected from fine row
- *    (2xc, 2yc, 2zc) (Section II-E, straight injection).
+ *    (2xc, 2yc, 2zc) (Section II-F, straight injection).
  */
 #ifndef HPCG_GB300_H
 #define HPCG_GB300_H
@@ -144,7 +144,7 @@ int hpcg_level_dims(hpcg_handle h, int level, int *dims_host);
 /* Colour of every row of `level` (Section III-A), int32 [n_level]. */
 int hpcg_get_colors(hpcg_handle h, int level, int *colors_dev, void *stream);
 /* Injection map of `level` -> level+1: f2c[c] = fine row of coarse row c,
- * int32 [n_{level+1}] (Section II-E). INVALID_ARG on the coarsest level. */
+ * int32 [n_{level+1}] (Section II-F). INVALID_ARG on the coarsest level. */
 int hpcg_get_f2c(hpcg_handle h, int level, int *f2c_dev, void *stream);
 /* Nonzeros of every row (8..27), int32 [n_level] (Section II-C). */
 int hpcg_get_row_nnz(hpcg_handle h, int level, int *nnz_dev, void *stream);
@@ -161,14 +161,14 @@ int hpcg_spmv(hpcg_handle h, int level, const double *x_dev, double *y_dev, void
 int hpcg_rbgs_color(hpcg_handle h, int level, int color, const double *r_dev, double *z_dev, void *stream);
 
 /* One smoother application on `level`: colours 0..7, then (symmetric option)
- * 7..0, in place on z (the smoother that replaces SGS, Sections II-D, III-A). */
+ * 7..0, in place on z (the smoother that replaces SGS, Sections II-E, III-A). */
 int hpcg_rbgs(hpcg_handle h, int level, const double *r_dev, double *z_dev, void *stream);
 
-/* Fused residual and restriction (Listing 1 lines 5-6, Section II-E):
+/* Fused residual and restriction (Listing 1's residual and restriction, Section II-F):
  * rc[c] = r[f2c[c]] - (A_level z)[f2c[c]]; r, z FP64 [n_level], rc [n_{level+1}]. */
 int hpcg_restrict_residual(hpcg_handle h, int level, const double *r_dev, const double *z_dev, double *rc_dev, void *stream);
 
-/* Refinement and correction (Listing 1 line 9): z[f2c[c]] += zc[c]; others unchanged. */
+/* Refinement and correction (Listing 1's coarse correction): z[f2c[c]] += zc[c]; others unchanged. */
 int hpcg_prolong_add(hpcg_handle h, int level, const double *zc_dev, double *z_dev, void *stream);
 
 /* z = M r: one V-cycle of Listing 1 from z = 0 on all levels, in the handle's

@@ -10,7 +10,7 @@ Functions follow the paper section by section (Scolari & Yzelman, "Effective
 implementation of the High Performance Conjugate Gradient benchmark on
 GraphBLAS"): input generation (Sec. II-B), CRS operator with separate A_diag
 (Sec. III-A), greedy colouring (Sec. III-A), red-black Gauss-Seidel colour
-steps (Listings 2 and 3), straight injection and its transpose (Sec. II-E,
+steps (Listings 2 and 3), straight injection and its transpose (Sec. II-F,
 III-B), the MG V-cycle (Listing 1) and preconditioned CG (Sec. II-C).
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py

@@ -125,7 +125,7 @@ static void greedy_color(orc_level *L) {
   L->ncolors = maxc;
 }
 
-/* Straight injection (Section II-E): coarse point (xc,yc,zc) takes the fine
+/* Straight injection (Section II-F): coarse point (xc,yc,zc) takes the fine
  * value at the lowest corner (2xc,2yc,2zc) of its octet.  Returns a new array
  * of ncx*ncy*ncz fine-row indices. */
 static int *make_f2c(int nfx, int nfy, int ncx, int ncy, int ncz) {
@@ -275,7 +275,7 @@ void orc_rbgs_color_step(const orc_problem *p, int l, int k, const double *r, do
 
 /* One smoother application.  The paper's listings show the forward pass
  * (colours 0..c-1, Listing 3's loop bound); the smoother it replaces, SGS
- * (Section II-D), follows the forward sweep by a backward sweep, and the
+ * (Section II-E), follows the forward sweep by a backward sweep, and the
  * replacement must keep the preconditioner symmetric.  Reading used here: one
  * application = forward colours 0..c-1 then backward colours c-1..0.  With
  * symmetric == 0 only the forward pass runs (ablation). */
@@ -286,14 +286,14 @@ void orc_rbgs(const orc_problem *p, int l, const double *r, double *z) {
     for (int k = L->ncolors - 1; k >= 0; --k) orc_rbgs_color_step(p, l, k, r, z);
 }
 
-/* Restriction by injection (Section II-E, III-B): rc[c] = v[f2c[c]]. */
+/* Restriction by injection (Section II-F, III-B): rc[c] = v[f2c[c]]. */
 void orc_restrict(const orc_problem *p, int l, const double *v, double *rc) {
   const orc_level *F = &p->lv[l];
   long nc = p->lv[l + 1].n;
   for (long c = 0; c < nc; ++c) rc[c] = v[F->f2c[c]];
 }
 
-/* Refinement = transpose of injection (Section II-E, III-B): adds the coarse
+/* Refinement = transpose of injection (Section II-F, III-B): adds the coarse
  * value at the injected fine point and zero elsewhere: z[f2c[c]] += zc[c]. */
 void orc_prolong_add(const orc_problem *p, int l, const double *zc, double *z) {
   const orc_level *F = &p->lv[l];

@@ -96,7 +96,7 @@ static __global__ void k_ell_build(EllGeom g, long nrows_padded, int *__restrict
 }
 
 // f2c[pc]: stored fine row of the fine point (2 xc, 2 yc, 2 zc) injected into
-// stored coarse row pc (Section II-E)
+// stored coarse row pc (Section II-F)
 static __global__ void k_ell_f2c(EllGeom gf, EllGeom gc, int *__restrict__ f2c) {
   const long pc = gtid();
   if (pc >= gc.n) return;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kEllThreads) k_ell_gs(long p0, long p1, int ma
   z[p] = v / d;
 }
 
-// rc = injection of r - A z (Section II-E), only at the injected rows
+// rc = injection of r - A z (Section II-F), only at the injected rows
 template <bool EXACT>
 __global__ void __launch_bounds__(kEllThreads) k_ell_restrict(long nc, const int *__restrict__ f2c, const int *__restrict__ col,
                                                               const double *__restrict__ val, const double *__restrict__ r,

@@ -4,7 +4,7 @@
 // has diagonal 26 (+kappa_i) and -1 to every in-grid neighbour, so no matrix is
 // read from HBM.  Colour classes are the parity classes of Section III-A's
 // greedy colouring; injection takes the even-coordinate point of each octet
-// (Section II-E).  T is double (FP64 path) or float (mixed-precision
+// (Section II-F).  T is double (FP64 path) or float (mixed-precision
 // preconditioner).  Every kernel takes the instance table of its level so that
 // one launch covers a whole batch; `st` (nullable) gates work per instance
 // once that instance's CG has converged.
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kBlock) k_gs_color(const Inst *__restrict__ ta
   }
 }
 
-// Fused residual + injection (Listing 1 lines 5-6): for every coarse row c with
+// Fused residual + injection (Listing 1's residual and restriction): for every coarse row c with
 // fine row f = (2xc,2yc,2zc): rc[c] = r[f] - (A z)[f].
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_restrict_residual(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count,
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBlock) k_restrict_residual(const Inst *__rest
   }
 }
 
-// Refinement + correction (Listing 1 line 9): z[f(c)] += zc[c].
+// Refinement + correction (Listing 1's coarse correction): z[f(c)] += zc[c].
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong_add(const Inst *__restrict__ tabf, const Inst *__restrict__ tabc, int count,
                                                         const T *__restrict__ zc, T *__restrict__ z,
@@ -425,7 +425,7 @@ __global__ void k_grad_kappa(long n, const double *__restrict__ lam, const doubl
 
 // ---------------------------------------------------------------------------
 // Setup kernels (Section II-B input generation, Section III-A colouring,
-// Section II-E injection), one thread per row.
+// Section II-F injection), one thread per row.
 __global__ void k_colors(int nx, int ny, int nz, int *__restrict__ out) {
   pdl_enter();
   const long n = (long)nx * ny * nz;

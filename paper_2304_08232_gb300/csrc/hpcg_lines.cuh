@@ -156,7 +156,7 @@ __device__ __forceinline__ void tsum2(const T *__restrict__ zg, int nx, int ny, 
 //
 // vmask: line classes whose z values are valid; the others count as zero (the
 // first forward sweep from z = 0).  rc (nullable): fused residual + injection
-// (Listing 1 lines 5-6) after the last step, for a run on class (0, 0) that
+// (Listing 1's residual and restriction) after the last step, for a run on class (0, 0) that
 // ends on even x: every injected fine row (2xc, 2yc, 2zc) lies on these lines,
 // its neighbour sum is P + z(x-1) + z(x+1) with values final for this
 // smoother application, so rc[c] = r - (A_ii z - that sum) is formed here.

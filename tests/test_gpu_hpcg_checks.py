@@ -1,4 +1,4 @@
-"""HPCG's symmetry test on the GPU path (Section II-D: the smoother replacing
+"""HPCG's symmetry test on the GPU path (Section III-A: the smoother replacing
 symmetric Gauss-Seidel must keep the preconditioner symmetric): x'Ay = y'Ax
 and x'My = y'Mx for random x, y, to rounding, with the symmetric smoother in
 both storage forms of the V-cycle; the forward-only ablation is not

@@ -2,7 +2,7 @@
 
 Operator: Section II-B/II-C (27-point stencil, 8..27 nonzeros per row);
 A_diag: Section III-A; greedy colouring with eight colours: Section III-A;
-straight injection and its transpose: Sections II-E and III-B.
+straight injection and its transpose: Sections II-F and III-B.
 """
 import numpy as np
 import pytest
