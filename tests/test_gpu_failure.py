@@ -59,7 +59,12 @@ def test_vcycle_timeout_status_then_recovery():
     from paper_2304_08232_gb300 import HpcgProblem, _lib
     lib = _lib.load()
     g = HpcgProblem(16, 16, 16, levels=4, precision="mixed", persistent=True)
+    # one line per block: the coarse-level kernel then has more than one block,
+    # so its grid barriers wait (a single block never waits, whatever the limit)
+    g.set_launch_shapes([[1, 1, 1, 1]] * 4)
     r = torch.ones(16 ** 3, dtype=torch.float64, device="cuda")
+    first = ctypes.c_int()
+    assert lib.hpcg_persistent_levels(g.h, ctypes.byref(first)) == 0 and first.value >= 1
     assert lib.hpcg_set_wait_limit(g.h, 0) == 0
     g.mg_vcycle(r)
     status = ctypes.c_int()
