@@ -26,6 +26,7 @@ def test_barrier_timeout_is_reported_and_context_recovers():
     from paper_2304_08232_gb300 import HpcgProblem, _lib
     lib = _lib.load()
     g = HpcgProblem(32, 32, 32, levels=4, persistent=True)
+    g.set_launch_shapes([[1, 1, 1, 1]] * 4)  # several blocks in the coarse-level kernel, so its barriers wait
     b = g.get_rhs()
     first = ctypes.c_int()
     assert lib.hpcg_persistent_levels(g.h, ctypes.byref(first)) == 0
