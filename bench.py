@@ -331,8 +331,10 @@ def ell_study(b, x_ref, dev, stream):
         return e0.elapsed_time(e1) / reps
 
     out = {}
-    for name, sorted_ in [("colour_sorted", True), ("natural_order", False)]:
-        e = HpcgEll(NX, NY, NZ, levels=LEVELS, colour_sorted=sorted_, device=dev)
+    for name, sorted_, bf16 in [("colour_sorted", True, False), ("natural_order", False, False),
+                                ("colour_sorted_bf16_values", True, True)]:
+        e = HpcgEll(NX, NY, NZ, levels=LEVELS, colour_sorted=sorted_, bf16_values=bf16, device=dev)
+        slot_b = (2 if bf16 else 8) + 4  # value + column
         rows, slices, _ = e.level_info(0)
         x = torch.zeros(n, dtype=torch.float64, device=dev)
         solve_ms = ev_ms(lambda: e.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x), 2)
@@ -340,9 +342,9 @@ def ell_study(b, x_ref, dev, stream):
         xs = e.to_stored(b)
         ys = torch.empty_like(xs)
         sp_ms = ev_ms(lambda: e.spmv(xs, out=ys), 10)
-        # algorithmic bytes of one SpMV: every slot (8-byte value + 4-byte
+        # algorithmic bytes of one SpMV: every slot (8- or 2-byte value + 4-byte
         # column, padding slots included) once, x once, y once
-        sp_bytes = slices * 27 * 32 * 12 + 16 * rows
+        sp_bytes = slices * 27 * 32 * slot_b + 16 * rows
         zs = torch.zeros_like(xs)
         sm_ms = ev_ms(lambda: e.rbgs(xs, zs), 5)
         # one symmetric application: 16 colour phases; algorithmic bytes of a
@@ -350,7 +352,7 @@ def ell_study(b, x_ref, dev, stream):
         # (z read and written), and the z of the other seven colours its rows
         # neighbour, once (the same count for both layouts: a masked phase in
         # natural order drags in slots of rows of other colours as well)
-        sm_bytes = 16 * (slices * 27 * 32 * 12 / 8 + 8 * 3 * rows / 8 + 8 * 7 * rows / 8)
+        sm_bytes = 16 * (slices * 27 * 32 * slot_b / 8 + 8 * 3 * rows / 8 + 8 * 7 * rows / 8)
         out[name] = {"ms_per_step": solve_ms, "max_abs_err_vs_ones": err,
                      "max_abs_diff_x_vs_matrix_free": float((x - x_ref).abs().max()),
                      "matrix_bytes": e.nbytes(), "spmv_ms": sp_ms, "spmv_bytes": sp_bytes,

@@ -326,17 +326,20 @@ int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const double *r_d
  * multiply-add), sums start from 0.0 in slot order, and the colour update is
  * (r_i - s_i + z_i d_i) / d_i with s_i including the diagonal (Listing 3), so
  * the level calls reproduce a plain sequential CRS evaluation bit for bit;
- * exact = 0 (faster) fuses the multiply-adds.
+ * exact = 0 (faster) fuses the multiply-adds.  bf16_values = 1 stores the
+ * values in BF16 (2 bytes instead of 8 per slot): 26, -1 and 0 are exact there,
+ * so every result is the same, bit for bit, as with FP64 values.
  *
  * Memory: hpcg_ell_setup allocates (cudaMalloc) about 12 * 27 bytes per row for
- * the matrix plus vectors and maps, on the current device (2.5 GB at 192^3 with
- * 4 levels); hpcg_ell_bytes reports the total.  Calls are ordered on `stream`;
+ * the matrix (6 * 27 with BF16 values) plus vectors and maps, on the current
+ * device (3.1 GB at 192^3 with 4 levels and FP64 values); hpcg_ell_bytes
+ * reports the total.  Calls are ordered on `stream`;
  * the handle serialises host threads.
  * Errors: INVALID_ARG for null or aliased pointers, a level or colour out of
  * range, and the grid rules of hpcg_setup; CUDA when an allocation or launch
  * fails. */
 typedef struct hpcg_ell_ctx *hpcg_ell_handle;
-int hpcg_ell_setup(int nx, int ny, int nz, int levels, int colour_sorted, int exact, hpcg_ell_handle *out);
+int hpcg_ell_setup(int nx, int ny, int nz, int levels, int colour_sorted, int exact, int bf16_values, hpcg_ell_handle *out);
 int hpcg_ell_destroy(hpcg_ell_handle h);
 int hpcg_ell_bytes(hpcg_ell_handle h, size_t *bytes);
 /* info_host[0] = rows, [1] = slices of 32 rows, [2..10] = cstart[0..8] (all zero when not sorted). */
@@ -344,7 +347,8 @@ int hpcg_ell_level_info(hpcg_ell_handle h, int level, long *info_host);
 /* perm_dev[p] (int32 [n], device) = natural row index of stored row p. */
 int hpcg_ell_permutation(hpcg_ell_handle h, int level, int *perm_dev, void *stream);
 /* Copies the slices: slot s of stored row p at ((p/32)*27 + s)*32 + p%32 of
- * col_dev (int32) and val_dev (FP64), each of slices*27*32 entries. */
+ * col_dev (int32) and val_dev (FP64, widened from BF16 storage), each of
+ * slices*27*32 entries. */
 int hpcg_ell_matrix(hpcg_ell_handle h, int level, int *col_dev, double *val_dev, void *stream);
 /* to_stored = 1: dst[p] = src[perm[p]]; 0: dst[perm[p]] = src[p] (FP64 [n], distinct buffers). */
 int hpcg_ell_permute(hpcg_ell_handle h, int level, int to_stored, const double *src_dev, double *dst_dev, void *stream);

@@ -61,7 +61,7 @@ SIGNATURES = {
     "hpcg_profile_iteration": (_i, [_vp, _vp, _vp, ctypes.POINTER(_d), _i, _vp]),
     "hpcg_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "hpcg_persistent_levels": (_i, [_vp, ctypes.POINTER(_i)]),
-    "hpcg_ell_setup": (_i, [_i, _i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "hpcg_ell_setup": (_i, [_i, _i, _i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
     "hpcg_ell_destroy": (_i, [_vp]),
     "hpcg_ell_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "hpcg_ell_level_info": (_i, [_vp, _i, ctypes.POINTER(_l)]),

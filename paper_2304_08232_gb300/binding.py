@@ -259,7 +259,7 @@ class HpcgEll:
     (P^T A P, hpcg_ell_setup); colour_sorted=False keeps the natural order.
     Level calls take vectors in the stored order (to_stored / to_natural)."""
 
-    def __init__(self, nx, ny, nz, levels=4, colour_sorted=True, exact=False, device=None):
+    def __init__(self, nx, ny, nz, levels=4, colour_sorted=True, exact=False, bf16_values=False, device=None):
         self.lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("HpcgEll needs a CUDA device")
@@ -267,8 +267,8 @@ class HpcgEll:
         self.dims, self.levels = (nx, ny, nz), levels
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            check(self.lib.hpcg_ell_setup(nx, ny, nz, levels, 1 if colour_sorted else 0, 1 if exact else 0, ctypes.byref(h)),
-                  "hpcg_ell_setup")
+            check(self.lib.hpcg_ell_setup(nx, ny, nz, levels, 1 if colour_sorted else 0, 1 if exact else 0, 1 if bf16_values else 0,
+                                          ctypes.byref(h)), "hpcg_ell_setup")
         self.h = h
         self.n = nx * ny * nz
 

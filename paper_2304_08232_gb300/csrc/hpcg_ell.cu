@@ -30,6 +30,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "hpcg.h"
@@ -43,7 +44,7 @@ struct EllLevel {
   EllGeom g;
   long nslices;
   int *col = nullptr;
-  double *val = nullptr;
+  void *val = nullptr;  // double or __nv_bfloat16 slots (hpcg_ell_ctx::bf16)
   double *diag = nullptr;
   int *perm = nullptr;
   int *f2c = nullptr;   // to the next coarser level (all levels but the last)
@@ -55,6 +56,7 @@ struct hpcg_ell_ctx {
   int levels;
   int sorted;
   int exact;
+  int bf16;  // operator values stored in BF16 (exact for 26, -1 and 0)
   EllLevel lv[kEllMaxLevels];
   // CG work vectors on level 0 (stored order) and scalars
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *ap = nullptr;
@@ -98,7 +100,7 @@ static int ell_build(hpcg_ell_ctx *h, int nx, int ny, int nz) {
     L.nslices = (g.n + kSlice - 1) / kSlice;
     const size_t slots = (size_t)L.nslices * kEllW * kSlice;
     TRY(ell_alloc(h, (void **)&L.col, slots * sizeof(int)));
-    TRY(ell_alloc(h, (void **)&L.val, slots * sizeof(double)));
+    TRY(ell_alloc(h, (void **)&L.val, slots * (h->bf16 ? sizeof(__nv_bfloat16) : sizeof(double))));
     TRY(ell_alloc(h, (void **)&L.diag, g.n * sizeof(double)));
     TRY(ell_alloc(h, (void **)&L.perm, g.n * sizeof(int)));
     if (l > 0) {
@@ -106,7 +108,10 @@ static int ell_build(hpcg_ell_ctx *h, int nx, int ny, int nz) {
       TRY(ell_alloc(h, (void **)&L.z, g.n * sizeof(double)));
     }
     const long rows = L.nslices * kSlice;
-    k_ell_build<<<blocks_for(rows), kEllThreads>>>(g, rows, L.col, L.val, L.diag, L.perm);
+    if (h->bf16)
+      k_ell_build<__nv_bfloat16><<<blocks_for(rows), kEllThreads>>>(g, rows, L.col, (__nv_bfloat16 *)L.val, L.diag, L.perm);
+    else
+      k_ell_build<double><<<blocks_for(rows), kEllThreads>>>(g, rows, L.col, (double *)L.val, L.diag, L.perm);
     CKL("k_ell_build");
   }
   for (int l = 0; l + 1 < h->levels; ++l) {
@@ -126,12 +131,28 @@ static int ell_build(hpcg_ell_ctx *h, int nx, int ny, int nz) {
 
 // ---------------------------------------------------------------------------
 // enqueue helpers (stored order)
+
+// Calls f with the (EXACT, value type) instance the handle uses:
+// f(std::integral_constant<bool, EXACT>, (const TV *)values).
+template <typename F>
+static void ell_dispatch(const hpcg_ell_ctx *h, const void *val, F &&f) {
+  if (h->bf16) {
+    if (h->exact)
+      f(std::true_type{}, (const __nv_bfloat16 *)val);
+    else
+      f(std::false_type{}, (const __nv_bfloat16 *)val);
+  } else {
+    if (h->exact)
+      f(std::true_type{}, (const double *)val);
+    else
+      f(std::false_type{}, (const double *)val);
+  }
+}
 static int ell_spmv(hpcg_ell_ctx *h, int l, const double *x, double *y, cudaStream_t s) {
   const EllLevel &L = h->lv[l];
-  if (h->exact)
-    k_ell_spmv<true><<<blocks_for(L.g.n), kEllThreads, 0, s>>>(L.g.n, L.col, L.val, x, y);
-  else
-    k_ell_spmv<false><<<blocks_for(L.g.n), kEllThreads, 0, s>>>(L.g.n, L.col, L.val, x, y);
+  ell_dispatch(h, L.val, [&](auto ex, auto val) {
+    k_ell_spmv<decltype(ex)::value><<<blocks_for(L.g.n), kEllThreads, 0, s>>>(L.g.n, L.col, val, x, y);
+  });
   CKL("k_ell_spmv");
   return HPCG_OK;
 }
@@ -146,10 +167,9 @@ static int ell_colour(hpcg_ell_ctx *h, int l, int k, const double *r, double *z,
     mask = -1;
   }
   if (p1 <= p0) return HPCG_OK;
-  if (h->exact)
-    k_ell_gs<true><<<blocks_for(p1 - p0), kEllThreads, 0, s>>>(p0, p1, mask, L.g, L.col, L.val, L.diag, r, z);
-  else
-    k_ell_gs<false><<<blocks_for(p1 - p0), kEllThreads, 0, s>>>(p0, p1, mask, L.g, L.col, L.val, L.diag, r, z);
+  ell_dispatch(h, L.val, [&](auto ex, auto val) {
+    k_ell_gs<decltype(ex)::value><<<blocks_for(p1 - p0), kEllThreads, 0, s>>>(p0, p1, mask, L.g, L.col, val, L.diag, r, z);
+  });
   CKL("k_ell_gs");
   return HPCG_OK;
 }
@@ -176,10 +196,9 @@ static int ell_mg(hpcg_ell_ctx *h, int l, const double *r, double *z, cudaStream
   TRY(ell_smoother(h, l, r, z, s));
   if (l == h->levels - 1) return HPCG_OK;
   EllLevel &C = h->lv[l + 1];
-  if (h->exact)
-    k_ell_restrict<true><<<blocks_for(C.g.n), kEllThreads, 0, s>>>(C.g.n, L.f2c, L.col, L.val, r, z, C.r);
-  else
-    k_ell_restrict<false><<<blocks_for(C.g.n), kEllThreads, 0, s>>>(C.g.n, L.f2c, L.col, L.val, r, z, C.r);
+  ell_dispatch(h, L.val, [&](auto ex, auto val) {
+    k_ell_restrict<decltype(ex)::value><<<blocks_for(C.g.n), kEllThreads, 0, s>>>(C.g.n, L.f2c, L.col, val, r, z, C.r);
+  });
   CKL("k_ell_restrict");
   TRY(ell_mg(h, l + 1, C.r, C.z, s));
   k_ell_prolong<<<blocks_for(C.g.n), kEllThreads, 0, s>>>(C.g.n, L.f2c, C.z, z);
@@ -203,7 +222,7 @@ static int ell_check_level(const hpcg_ell_ctx *h, int l) { return (l < 0 || l >=
 // C ABI
 extern "C" {
 
-int hpcg_ell_setup(int nx, int ny, int nz, int levels, int colour_sorted, int exact, hpcg_ell_handle *out) {
+int hpcg_ell_setup(int nx, int ny, int nz, int levels, int colour_sorted, int exact, int bf16_values, hpcg_ell_handle *out) {
   if (!out) return HPCG_ERR_INVALID_ARG;
   *out = nullptr;
   if (levels < 1 || levels > kEllMaxLevels) return HPCG_ERR_INVALID_ARG;
@@ -215,6 +234,7 @@ int hpcg_ell_setup(int nx, int ny, int nz, int levels, int colour_sorted, int ex
   h->levels = levels;
   h->sorted = colour_sorted ? 1 : 0;
   h->exact = exact ? 1 : 0;
+  h->bf16 = bf16_values ? 1 : 0;
   const int rc = ell_build(h, nx, ny, nz);
   if (rc != HPCG_OK) {
     ell_free(h);
@@ -264,7 +284,13 @@ int hpcg_ell_matrix(hpcg_ell_handle h, int level, int *col_dev, double *val_dev,
   const EllLevel &L = h->lv[level];
   const size_t slots = (size_t)L.nslices * kEllW * kSlice;
   CK(cudaMemcpyAsync(col_dev, L.col, slots * sizeof(int), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
-  CK(cudaMemcpyAsync(val_dev, L.val, slots * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  if (h->bf16) {
+    k_ell_widen<__nv_bfloat16><<<blocks_for((long)slots), kEllThreads, 0, (cudaStream_t)stream>>>((long)slots, (const __nv_bfloat16 *)L.val,
+                                                                                                   val_dev);
+    CKL("k_ell_widen");
+  } else {
+    CK(cudaMemcpyAsync(val_dev, L.val, slots * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  }
   return HPCG_OK;
 }
 

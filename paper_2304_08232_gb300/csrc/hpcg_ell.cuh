@@ -4,6 +4,7 @@
 // whole-grid engine (hpcg_ell.cu) and the two-sub-domain engine
 // (hpcg_split.cu).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -53,18 +54,36 @@ __device__ __forceinline__ void ell_coords(const EllGeom &g, long p, int &x, int
 // address of slot s of stored row p
 __device__ __forceinline__ long slot_of(long p, int s) { return ((p >> 5) * kEllW + s) * kSlice + (p & 31); }
 
+// Stored operator values: FP64, or BF16 (the values 26, -1 and 0 are exact in
+// BF16, so a BF16 matrix gives the same products as an FP64 one).  A BF16 value
+// is widened to FP64 on the integer pipe by moving its sign, exponent and
+// 7 mantissa bits into the FP64 fields (a conversion instruction would occupy
+// the FP64 pipe, which the products already fill); this covers zero and the
+// normal numbers, the values the operator stores.
+__device__ __forceinline__ double ell_val(const double *p) { return __ldg(p); }
+__device__ __forceinline__ double ell_val(const __nv_bfloat16 *p) {
+  const unsigned int u = __ldg(reinterpret_cast<const unsigned short *>(p));
+  const unsigned int e = (u >> 7) & 0xFFu;
+  const unsigned long long bits = ((unsigned long long)(u >> 15) << 63) | ((unsigned long long)(e + 1023u - 127u) << 52) |
+                                  ((unsigned long long)(u & 0x7Fu) << 45);
+  return e == 0u ? 0.0 : __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ void ell_set(double *p, double v) { *p = v; }
+__device__ __forceinline__ void ell_set(__nv_bfloat16 *p, double v) { *p = __float2bfloat16_rn((float)v); }
+
 __device__ __forceinline__ long gtid() { return blockIdx.x * (long)blockDim.x + threadIdx.x; }
 
 // One thread per stored row (padding rows of the last slice included): the
 // row's slots, the diagonal and the natural index.
-static __global__ void k_ell_build(EllGeom g, long nrows_padded, int *__restrict__ col, double *__restrict__ val, double *__restrict__ diag,
+template <typename TV>
+__global__ void k_ell_build(EllGeom g, long nrows_padded, int *__restrict__ col, TV *__restrict__ val, double *__restrict__ diag,
                             int *__restrict__ perm) {
   const long p = gtid();
   if (p >= nrows_padded) return;
   if (p >= g.n) {
     for (int s = 0; s < kEllW; ++s) {
       col[slot_of(p, s)] = 0;
-      val[slot_of(p, s)] = 0.0;
+      ell_set(val + slot_of(p, s), 0.0);
     }
     return;
   }
@@ -84,14 +103,14 @@ static __global__ void k_ell_build(EllGeom g, long nrows_padded, int *__restrict
         if (xx < 0 || xx >= g.nx) continue;
         const bool self = dx == 0 && dy == 0 && dz == 0;
         col[slot_of(p, s)] = (int)ell_index(g, xx, yy, zz);
-        val[slot_of(p, s)] = self ? 26.0 : -1.0;
+        ell_set(val + slot_of(p, s), self ? 26.0 : -1.0);
         ++s;
       }
     }
   }
   for (; s < kEllW; ++s) {
     col[slot_of(p, s)] = (int)p;
-    val[slot_of(p, s)] = 0.0;
+    ell_set(val + slot_of(p, s), 0.0);
   }
 }
 
@@ -106,21 +125,21 @@ static __global__ void k_ell_f2c(EllGeom gf, EllGeom gc, int *__restrict__ f2c) 
 }
 
 // sum over the slots of row p of val * v[col]
-template <bool EXACT>
-__device__ __forceinline__ double row_sum(long p, const int *__restrict__ col, const double *__restrict__ val, const double *__restrict__ v) {
+template <bool EXACT, typename TV>
+__device__ __forceinline__ double row_sum(long p, const int *__restrict__ col, const TV *__restrict__ val, const double *__restrict__ v) {
   const long base = ((p >> 5) * kEllW) * kSlice + (p & 31);
   double s = 0.0;
 #pragma unroll
   for (int k = 0; k < kEllW; ++k) {
-    const double a = __ldg(val + base + k * kSlice);
+    const double a = ell_val(val + base + k * kSlice);
     const double b = v[__ldg(col + base + k * kSlice)];
     s = EXACT ? __dadd_rn(s, __dmul_rn(a, b)) : fma(a, b, s);
   }
   return s;
 }
 
-template <bool EXACT>
-__global__ void __launch_bounds__(kEllThreads) k_ell_spmv(long n, const int *__restrict__ col, const double *__restrict__ val,
+template <bool EXACT, typename TV>
+__global__ void __launch_bounds__(kEllThreads) k_ell_spmv(long n, const int *__restrict__ col, const TV *__restrict__ val,
                                                           const double *__restrict__ x, double *__restrict__ y) {
   const long p = gtid();
   if (p < n) y[p] = row_sum<EXACT>(p, col, val, x);
@@ -130,9 +149,9 @@ __global__ void __launch_bounds__(kEllThreads) k_ell_spmv(long n, const int *__r
 // colour k (all of them when the rows are grouped; mask >= 0 tests the colour
 // of each row in natural order).  Rows of one colour have no neighbour of
 // their colour, so they update independently.
-template <bool EXACT>
+template <bool EXACT, typename TV>
 __global__ void __launch_bounds__(kEllThreads) k_ell_gs(long p0, long p1, int mask, EllGeom g, const int *__restrict__ col,
-                                                        const double *__restrict__ val, const double *__restrict__ diag,
+                                                        const TV *__restrict__ val, const double *__restrict__ diag,
                                                         const double *__restrict__ r, double *__restrict__ z) {
   const long p = p0 + gtid();
   if (p >= p1) return;
@@ -147,9 +166,9 @@ __global__ void __launch_bounds__(kEllThreads) k_ell_gs(long p0, long p1, int ma
 }
 
 // rc = injection of r - A z (Section II-F), only at the injected rows
-template <bool EXACT>
+template <bool EXACT, typename TV>
 __global__ void __launch_bounds__(kEllThreads) k_ell_restrict(long nc, const int *__restrict__ f2c, const int *__restrict__ col,
-                                                              const double *__restrict__ val, const double *__restrict__ r,
+                                                              const TV *__restrict__ val, const double *__restrict__ r,
                                                               const double *__restrict__ z, double *__restrict__ rc) {
   const long pc = gtid();
   if (pc >= nc) return;
@@ -164,6 +183,12 @@ static __global__ void __launch_bounds__(kEllThreads) k_ell_prolong(long nc, con
   if (pc >= nc) return;
   const long pf = f2c[pc];
   z[pf] = __dadd_rn(z[pf], zc[pc]);
+}
+
+template <typename TV>
+__global__ void k_ell_widen(long n, const TV *__restrict__ v, double *__restrict__ out) {
+  const long i = gtid();
+  if (i < n) out[i] = ell_val(v + i);
 }
 
 static __global__ void k_ell_fill(long n, double v, double *__restrict__ a) {

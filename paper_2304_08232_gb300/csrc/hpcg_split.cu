@@ -259,9 +259,9 @@ static int sp_spmv(hpcg_split_ctx *h, int l, double *const x[kDomains], double *
   for (int d = 0; d < kDomains; ++d) {
     const SplitDom &D = h->lv[l].d[d];
     if (h->exact)
-      k_ell_spmv<true><<<nblk(D.nloc), kEllThreads, 0, s>>>(D.nloc, D.col, D.val, x[d], y[d]);
+      k_ell_spmv<true, double><<<nblk(D.nloc), kEllThreads, 0, s>>>(D.nloc, D.col, D.val, x[d], y[d]);
     else
-      k_ell_spmv<false><<<nblk(D.nloc), kEllThreads, 0, s>>>(D.nloc, D.col, D.val, x[d], y[d]);
+      k_ell_spmv<false, double><<<nblk(D.nloc), kEllThreads, 0, s>>>(D.nloc, D.col, D.val, x[d], y[d]);
     CKL("k_ell_spmv");
   }
   return HPCG_OK;
@@ -277,9 +277,9 @@ static int sp_smoother(hpcg_split_ctx *h, int l, double *const r[kDomains], doub
       const long p0 = D.cstart[k], p1 = D.cstart[k + 1];
       if (p1 <= p0) continue;
       if (h->exact)
-        k_ell_gs<true><<<nblk(p1 - p0), kEllThreads, 0, s>>>(p0, p1, -1, none, D.col, D.val, D.diag, r[d], z[d]);
+        k_ell_gs<true, double><<<nblk(p1 - p0), kEllThreads, 0, s>>>(p0, p1, -1, none, D.col, D.val, D.diag, r[d], z[d]);
       else
-        k_ell_gs<false><<<nblk(p1 - p0), kEllThreads, 0, s>>>(p0, p1, -1, none, D.col, D.val, D.diag, r[d], z[d]);
+        k_ell_gs<false, double><<<nblk(p1 - p0), kEllThreads, 0, s>>>(p0, p1, -1, none, D.col, D.val, D.diag, r[d], z[d]);
       CKL("k_ell_gs");
     }
     TRY(sp_exchange(h, l, z, k, k + 1, s));  // the values of colour k just updated
@@ -305,9 +305,9 @@ static int sp_mg(hpcg_split_ctx *h, int l, double *const r[kDomains], double *co
     rc[d] = C.d[d].r;
     zc[d] = C.d[d].z;
     if (h->exact)
-      k_ell_restrict<true><<<nblk(nc), kEllThreads, 0, s>>>(nc, D.f2c, D.col, D.val, r[d], z[d], rc[d]);
+      k_ell_restrict<true, double><<<nblk(nc), kEllThreads, 0, s>>>(nc, D.f2c, D.col, D.val, r[d], z[d], rc[d]);
     else
-      k_ell_restrict<false><<<nblk(nc), kEllThreads, 0, s>>>(nc, D.f2c, D.col, D.val, r[d], z[d], rc[d]);
+      k_ell_restrict<false, double><<<nblk(nc), kEllThreads, 0, s>>>(nc, D.f2c, D.col, D.val, r[d], z[d], rc[d]);
     CKL("k_ell_restrict");
   }
   TRY(sp_mg(h, l + 1, rc, zc, s));

@@ -18,10 +18,10 @@ pytestmark = pytest.mark.gpu
 GRIDS = [((16, 16, 16), 4), ((6, 10, 4), 2), ((24, 8, 16), 3), ((2, 2, 2), 1), ((5, 3, 7), 1)]
 
 
-def _ell(dims, levels, sorted_=True, exact=False):
+def _ell(dims, levels, sorted_=True, exact=False, bf16=False):
     from paper_2304_08232_gb300 import HpcgEll
     need_gpu()
-    return HpcgEll(*dims, levels=levels, colour_sorted=sorted_, exact=exact)
+    return HpcgEll(*dims, levels=levels, colour_sorted=sorted_, exact=exact, bf16_values=bf16)
 
 
 @pytest.mark.parametrize("dims,levels", GRIDS)
@@ -104,6 +104,34 @@ def test_fma_kernels_within_fp64_tolerance_and_layout_independent(dims, levels):
     zn = host(en.mg_vcycle(dev(r)))
     assert normwise(zs, o.mg(r)) <= TOL64
     np.testing.assert_array_equal(zs, zn)
+
+
+@pytest.mark.parametrize("dims,levels", [((16, 16, 16), 4), ((6, 10, 4), 2), ((5, 3, 7), 1)])
+@pytest.mark.parametrize("exact", [True, False])
+def test_bf16_values_give_the_same_bits(dims, levels, exact):
+    """26, -1 and 0 are exact in BF16: the BF16-valued matrix stores the same
+    operator in a quarter of the value bytes and every level call and the solve
+    give the same bits as with FP64 values."""
+    e8, e2 = _ell(dims, levels, True, exact), _ell(dims, levels, True, exact, bf16=True)
+    assert e2.nbytes() < e8.nbytes()
+    for l in range(levels):
+        c8, v8 = (host(t) for t in e8.matrix(l))
+        c2, v2 = (host(t) for t in e2.matrix(l))
+        np.testing.assert_array_equal(c2, c8)
+        np.testing.assert_array_equal(v2, v8)
+        n = e8.level_info(l)[0]
+        x = dev(normal(n, 56 + l))
+        np.testing.assert_array_equal(host(e2.spmv(x, l)), host(e8.spmv(x, l)))
+        r, z = dev(normal(n, 60 + l)), dev(normal(n, 64 + l))
+        np.testing.assert_array_equal(host(e2.rbgs(r, z.clone(), l)), host(e8.rbgs(r, z.clone(), l)))
+    n = e8.n
+    r = dev(normal(n, 68))
+    np.testing.assert_array_equal(host(e2.mg_vcycle(r)), host(e8.mg_vcycle(r)))
+    b = dev(normal(n, 69))
+    x8, s8 = e8.pcg_solve(b, max_iters=20, tol=0.0)
+    x2, s2 = e2.pcg_solve(b, max_iters=20, tol=0.0)
+    np.testing.assert_array_equal(host(x2), host(x8))
+    np.testing.assert_array_equal(np.asarray(s2.history), np.asarray(s8.history))
 
 
 @pytest.mark.parametrize("exact", [True, False])
