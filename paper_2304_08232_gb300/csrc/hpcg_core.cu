@@ -968,7 +968,10 @@ static int enqueue_finalize_lines(hpcg_ctx *h, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // PCG (Section II-C), HPCG iteration order; every kernel is gated per instance
 // by the device-side `done` flag, so iterations enqueued after convergence are
-// no-ops and the host may run ahead of the device.
+// no-ops and the host may run ahead of the device.  Each iteration's
+// x += alpha p is deferred to the next iteration's p update (which reads the
+// same old p); a solve ends with the pending one (enqueue_x_pending), and a
+// mixed-precision residual replacement applies it before forming b - A x.
 static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_iters, double tol, cudaStream_t s) {
   std::vector<CgState> init(h->count);
   for (auto &c : init) {
