@@ -93,6 +93,10 @@ typedef struct {
   int restart_every; /* mixed precision: also replace the recurrence residual by b - A x (FP64) after
                         every this many iterations, besides the stall rule (no 1% progress in 3
                         iterations); 0 (default): on stalls only */
+  int bfp_split;     /* with block_fp: levels whose x-lines have 65-256 points run their colour steps
+                        with one warp per 64-point chunk of a line (neighbours across chunks through
+                        shared memory; same z bits, r.z partials summed chunk by chunk); 0 (default):
+                        one warp per line */
 } hpcg_options;
 
 typedef struct {

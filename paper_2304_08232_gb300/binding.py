@@ -59,7 +59,7 @@ class HpcgProblem:
 
     def __init__(self, nx, ny, nz, levels=4, precision="fp64", kappa=None, pre_sweeps=1, post_sweeps=1,
                  symmetric=True, max_rhs=0, check_every=1, persistent=False, fixed_point=True, pdl=True, block_fp=True,
-                 cluster_tail=False, restart_every=0, device=None):
+                 cluster_tail=False, restart_every=0, bfp_split=False, device=None):
         self.lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("HpcgProblem needs a CUDA device")
@@ -78,6 +78,7 @@ class HpcgProblem:
         opt.block_fp = 1 if block_fp else 0
         opt.cluster_tail = 1 if cluster_tail else 0
         opt.restart_every = int(restart_every)
+        opt.bfp_split = 1 if bfp_split else 0
         self.dims = (nx, ny, nz)
         self.levels = levels
         self.precision = precision

@@ -374,6 +374,269 @@ __global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ t
                           zout, dpart, zqc, zec, tabcp);
 }
 
+// ---------------------------------------------------------------------------
+// The same colour-pair runs with each x-line split over W warps, one 64-point
+// chunk each (x in [64k, 64k + 64), the lane holding the pair x = 64k + 2 lane,
+// + 1).  One warp per line holds W pairs per lane (122 registers at W = 3: two
+// 8-warp blocks per SM, each warp mostly waiting on its loads); one pair per
+// lane needs far fewer registers, so more warps wait at a time.  What the
+// one-warp kernel moves between chunks inside a warp goes through shared
+// memory here: the column sums beside each chunk boundary, the line's largest
+// exponents of r and 1 / A_ii, the value beside the boundary before each
+// colour step, the OR of the magnitudes that sets the stored exponent, and
+// the chunk partials of r.z (summed in chunk order, so that partial differs in
+// rounding from the one-warp kernel's; z, its exponents and the restricted
+// residual are the same bits).
+//
+// Every warp of a block passes the same sequence of block barriers (one after
+// the column sums, one per colour step, one for the magnitudes, one for the
+// r.z partials when they are asked for): the only early exits (no planes,
+// converged instance) hold for the whole block, and lines past the grid's
+// edge or with non-finite values skip loads, arithmetic and stores between
+// barriers, never a barrier.
+constexpr int kBfpSplitMaxLines = 8;  // lines per block (the autotuner's largest)
+
+template <int W>
+__global__ void __launch_bounds__(1024)
+    k_gs_lines_bfp_split(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa, int steps, int vmask,
+                         const double *__restrict__ r, long long *__restrict__ zq, int *__restrict__ ze, const double *__restrict__ invd,
+                         const CgState *__restrict__ st, const Inst *__restrict__ tabc, double *__restrict__ rc,
+                         const double *__restrict__ kap, double *__restrict__ zout, double *__restrict__ dpart,
+                         const long long *__restrict__ zqc, const int *__restrict__ zec, const Inst *__restrict__ tabcp, const Inst g1) {
+  pdl_enter();
+  __shared__ long long s_ce[kBfpSplitMaxLines][W], s_co[kBfpSplitMaxLines][W];  // a chunk's first ce, last co
+  __shared__ int s_er[kBfpSplitMaxLines][W], s_id[kBfpSplitMaxLines][W];         // a chunk's largest r and 1/A_ii exponents
+  __shared__ long long s_o[kBfpSplitMaxLines][W], s_e[kBfpSplitMaxLines][W];     // a chunk's last odd, first even value
+  __shared__ unsigned s_mhi[kBfpSplitMaxLines][W], s_mlo[kBfpSplitMaxLines][W];
+  __shared__ double s_rz[kBfpSplitMaxLines][W];
+  const int lane = threadIdx.x;
+  const int k = threadIdx.y % W;   // chunk of the line
+  const int wy = threadIdx.y / W;  // line of the block
+  const int blk = blockIdx.x;
+  const int ii = count == 1 ? 0 : find_inst<4>(tab, count, blk);
+  const Inst g = count == 1 ? g1 : tab[ii];
+  const int cy = (g.ny - py + 1) / 2, cz = (g.nz - pz + 1) / 2;
+  const int nby = (half_up(g.ny) + lpc - 1) / lpc;
+  const int lb = blk - g.blk_line;
+  const int j = (lb % nby) * lpc + wy;
+  const int m0 = (lb / nby) * zc;
+  const int m1 = min(m0 + zc, cz);
+  if (m0 >= m1) return;           // the whole block
+  if (st && st[ii].done) return;  // the whole block: a block belongs to one instance
+  const bool lok = j < cy;        // this line lies inside the grid
+  const int y = lok ? 2 * j + py : py;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long sxy = (long)nx * ny;
+  long long *qg = zq + g.off;
+  int *eg = ze + g.poff;
+  const double *rg = r + g.off;
+  const int xe = 64 * k + 2 * lane;  // this lane's pair
+  const bool xin = lok && xe < nx;
+  const bool vy = (vmask >> line_class(y + 1, pz)) & 1;
+  const bool ym = lok && y - 1 >= 0 && vy, yp = lok && y + 1 < ny && vy;
+  const bool own_valid = lok && ((vmask >> line_class(y, pz)) & 1);
+  const bool vyo = (vmask >> line_class(y + 1, pz + 1)) & 1;
+  const bool vy0 = (vmask >> line_class(y, pz + 1)) & 1;
+  auto ldq = [&](const long long *line, bool ok, long long &e, long long &o) {
+    if (ok && xin) {
+      const longlong2 v = __ldg(reinterpret_cast<const longlong2 *>(line + xe));
+      e = v.x;
+      o = v.y;
+    } else {
+      e = 0;
+      o = 0;
+    }
+  };
+  // sum over lines y-1, y, y+1 of plane zz at the largest of their exponents
+  auto plane = [&](int zz, long long &te, long long &to) -> int {
+    const bool zin = lok && zz >= 0 && zz < nz;
+    const bool oka = zin && y - 1 >= 0 && vyo, okb = zin && vy0, okd = zin && y + 1 < ny && vyo;
+    const long li = (long)zz * ny + y;
+    const int ea = oka ? __ldg(eg + li - 1) : kFxMinE;
+    const int eb = okb ? __ldg(eg + li) : kFxMinE;
+    const int ed = okd ? __ldg(eg + li + 1) : kFxMinE;
+    const int et = max(max(ea, eb), ed);
+    const long long *la = qg + (long)zz * sxy + (long)(y - 1) * nx;
+    long long ae, ao, be, bo, de, d_o;
+    ldq(la, oka, ae, ao);
+    ldq(la + nx, okb, be, bo);
+    ldq(la + 2 * nx, okd, de, d_o);
+    te = (shr_q(ae, et - ea) + shr_q(be, et - eb)) + shr_q(de, et - ed);
+    to = (shr_q(ao, et - ea) + shr_q(bo, et - eb)) + shr_q(d_o, et - ed);
+    return et;
+  };
+  long long tpe, tpo;
+  int Ec = plane(2 * m0 + pz - 1, tpe, tpo);
+  for (int m = m0; m < m1; ++m) {
+    const int zz = 2 * m + pz;
+    long long te, to;
+    const int et = plane(zz + 1, te, to);
+    const long li = (long)zz * ny + y;
+    const long rowbase = (long)zz * sxy + (long)y * nx;
+    const int eu = ym ? __ldg(eg + li - 1) : kFxMinE;
+    const int ew = yp ? __ldg(eg + li + 1) : kFxMinE;
+    int eo = own_valid ? eg[li] : kFxMinE;
+    long long ue, uo, we, wo, qe = 0, qo = 0;
+    ldq(qg + rowbase - nx, ym, ue, uo);
+    ldq(qg + rowbase + nx, yp, we, wo);
+    if (own_valid && xin) {  // own line: written only by this warp
+      const longlong2 v = *reinterpret_cast<const longlong2 *>(qg + rowbase + xe);
+      qe = v.x;
+      qo = v.y;
+    }
+    if (zqc && lok) {  // refinement fused into this run (see gs_bfp_block)
+      const Inst gc = tabcp[ii];
+      const long lic = (long)(zz >> 1) * gc.ny + (y >> 1);
+      const int e_c = __ldg(zec + gc.poff + lic);
+      const int Sp = max(eo, e_c) + 1;
+      const long long cv = xin ? __ldg(zqc + gc.off + lic * gc.nx + (xe >> 1)) : 0;
+      qe = shr_q(qe, Sp - eo) + shr_q(cv, Sp - e_c);
+      qo = shr_q(qo, Sp - eo);
+      eo = (eo > kFxMaxE || e_c > kFxMaxE) ? kBfpNaN : Sp;
+    }
+    double rE = 0.0, rO = 0.0;
+    if (xin) {
+      const double2 v = __ldg(reinterpret_cast<const double2 *>(rg + rowbase + xe));
+      rE = v.x;
+      rO = v.y;
+    }
+    const int E = max(max(Ec, et), max(eu, ew));
+    const long long ce = (shr_q(tpe, E - Ec) + shr_q(te, E - et)) + (shr_q(ue, E - eu) + shr_q(we, E - ew));
+    const long long co = (shr_q(tpo, E - Ec) + shr_q(to, E - et)) + (shr_q(uo, E - eu) + shr_q(wo, E - ew));
+    tpe = te;
+    tpo = to;
+    Ec = et;
+    int erc = max(kFxMinE, max(fx_exp(rE), fx_exp(rO)));
+    erc = warp_max(erc);
+    int idc = 0;
+    if (invd) {
+      if (xin) idc = max(fx_exp(invd[g.off + rowbase + xe]), fx_exp(invd[g.off + rowbase + xe + 1]));
+      idc = warp_max(idc);
+    }
+    if (lane == 0) {
+      s_ce[wy][k] = ce;
+      s_er[wy][k] = erc;
+      s_id[wy][k] = idc;
+    }
+    if (lane == 31) s_co[wy][k] = co;
+    __syncthreads();
+    int er = s_er[wy][0], idx = s_id[wy][0];
+#pragma unroll
+    for (int kk = 1; kk < W; ++kk) {
+      er = max(er, s_er[wy][kk]);
+      idx = max(idx, s_id[wy][kk]);
+    }
+    long long PE, PO;
+    {
+      long long sh = __shfl_up_sync(kFull, co, 1);
+      if (lane == 0) sh = k > 0 ? s_co[wy][k - 1] : 0LL;  // column x-1 of an even x
+      PE = (sh + ce) + co;
+      sh = __shfl_down_sync(kFull, ce, 1);
+      if (lane == 31) sh = k + 1 < W ? s_ce[wy][k + 1] : 0LL;  // column x+1 of an odd x
+      PO = (ce + co) + sh;
+    }
+    const int S = max(E + 5, max(er, eo)) + 2 + 3 * max(0, idx - 1021);
+    const int sout = (invd && idx > 1018) ? S : S - 3;
+    const bool bad = E > kFxMaxE || er > kFxMaxE || eo > kFxMaxE || S > kFxMaxE + 8;  // the same for the whole line
+    const bool act = lok && !bad;
+    long long re = 0, ro = 0, oE = 0, oO = 0, sE = 0, sO = 0, nbl = 0;
+    if (act) {
+      re = fx_of(rE, S) + shr_q(PE, S - E);
+      ro = fx_of(rO, S) + shr_q(PO, S - E);
+      oE = shr_q(qe, S - eo);
+      oO = shr_q(qo, S - eo);
+    }
+    const int down = S - sout;
+    for (int s = 0; s < steps; ++s) {
+      const int q = (s & 1) ? 1 - pa : pa;
+      if (q == 0) {
+        if (lane == 31) s_o[wy][k] = oO;
+        __syncthreads();
+        long long nb = __shfl_up_sync(kFull, oO, 1);
+        if (lane == 0) nb = k > 0 ? s_o[wy][k - 1] : 0LL;  // O at x - 1 of this even x
+        nbl = nb;
+        if (act && xe < nx) {
+          sE = bfp_new_value((re + nb) + oO, S, sout, invd, g.off + rowbase + xe);
+          oE = shr_q(sE, down);
+        }
+      } else {
+        if (lane == 0) s_e[wy][k] = oE;
+        __syncthreads();
+        long long nb = __shfl_down_sync(kFull, oE, 1);
+        if (lane == 31) nb = k + 1 < W ? s_e[wy][k + 1] : 0LL;  // E at x + 1 of this odd x
+        if (act && xe + 1 < nx) {
+          sO = bfp_new_value((ro + oE) + nb, S, sout, invd, g.off + rowbase + xe + 1);
+          oO = shr_q(sO, down);
+        }
+      }
+    }
+    // stored exponent: the line's largest |q| moved up to bit 57 (see gs_bfp_block)
+    const unsigned long long mag = (sE < 0 ? 0ULL - (unsigned long long)sE : (unsigned long long)sE) |
+                                   (sO < 0 ? 0ULL - (unsigned long long)sO : (unsigned long long)sO);
+    const unsigned chi = __reduce_or_sync(kFull, (unsigned)(mag >> 32)), clo = __reduce_or_sync(kFull, (unsigned)mag);
+    if (lane == 0) {
+      s_mhi[wy][k] = chi;
+      s_mlo[wy][k] = clo;
+    }
+    __syncthreads();
+    unsigned mhi = 0, mlo = 0;
+#pragma unroll
+    for (int kk = 0; kk < W; ++kk) {
+      mhi |= s_mhi[wy][kk];
+      mlo |= s_mlo[wy][kk];
+    }
+    const int lz = mhi ? __clz(mhi) : 32 + __clz(mlo);
+    const int up = min(max(lz - 6, 0), sout - kFxMinE);
+    double rz = 0.0;
+    if (lok && bad) {
+      if (xin) {
+        *reinterpret_cast<longlong2 *>(qg + rowbase + xe) = make_longlong2(0, 0);
+        if (zout) *reinterpret_cast<double2 *>(zout + g.off + rowbase + xe) = make_double2(bfp_nan(), bfp_nan());
+      }
+      if (k == 0 && lane == 0) eg[li] = kBfpNaN;
+      if (rc && xin) {
+        const Inst gc = tabc[ii];
+        rc[gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx + (xe >> 1)] = bfp_nan();
+      }
+      rz = bfp_nan();
+    } else if (act) {
+      if (xin) {
+        *reinterpret_cast<longlong2 *>(qg + rowbase + xe) =
+            make_longlong2((long long)((unsigned long long)sE << up), (long long)((unsigned long long)sO << up));
+        if (zout) {
+          const double ze_ = fx_to_double(sE, sout), zo_ = fx_to_double(sO, sout);
+          *reinterpret_cast<double2 *>(zout + g.off + rowbase + xe) = make_double2(ze_, zo_);
+          rz = rE * ze_ + rO * zo_;
+        }
+      }
+      if (k == 0 && lane == 0) eg[li] = sout - up;
+      if (rc && xin) {  // r - A z at the even points (the run ends on even x: nbl is the final O at x - 1)
+        const Inst gc = tabc[ii];
+        const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
+        const long long t = (re + nbl) + oO;
+        double res;
+        if (!kap)
+          res = fx_to_double(4 * t - 13 * sE, S - 2);
+        else
+          res = fx_to_double(t, S) - (26.0 + kap[g.off + rowbase + xe]) * fx_to_double(sE, sout);
+        rc[cbase + (xe >> 1)] = res;
+      }
+    }
+    if (zout && dpart) {  // per-line partial of r.z: lanes by a fixed shuffle tree, then chunks in order
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rz += __shfl_down_sync(kFull, rz, o);
+      if (lane == 0) s_rz[wy][k] = rz;
+      __syncthreads();
+      if (lok && k == 0 && lane == 0) {
+        double tot = s_rz[wy][0];
+#pragma unroll
+        for (int kk = 1; kk < W; ++kk) tot += s_rz[wy][kk];
+        dpart[g.poff + li] = tot;
+      }
+    }
+  }
+}
+
 // Refinement z_f <- z_f + R^T z_c on the block-floating-point vectors for
 // coarse line wl (all instances' lines numbered in order), which feeds the
 // even points of fine line (2 yc, 2 zc).  The fine line moves to exponent

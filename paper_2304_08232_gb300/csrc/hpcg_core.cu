@@ -747,7 +747,16 @@ static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s
 template <int NC>
 static void launch_gs_bfp(const LevelData &L, int count, int py, int pz, int pa, int steps, int vmask, const double *r, const double *invd,
                           const CgState *st, const Inst *tabc, double *rc, const double *kap, double *zout, double *dpart,
-                          const LevelData *C, cudaStream_t s) {
+                          const LevelData *C, cudaStream_t s, bool split) {
+  if constexpr (NC >= 2 && NC <= 4) {
+    // lines of 2-4 chunks: one warp per 64-point chunk (k_gs_lines_bfp_split)
+    if (split && L.tab.line_lpc <= kBfpSplitMaxLines) {
+      launch_k(k_gs_lines_bfp_split<NC>, dim3(L.tab.nblk_line), dim3(32, NC * L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc,
+               L.tab.line_zc, py, pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart,
+               C ? (const long long *)C->zq : nullptr, C ? (const int *)C->ze : nullptr, C ? C->tab.inst : nullptr, L.inst[0]);
+      return;
+    }
+  }
   launch_k(k_gs_lines_bfp<NC>, dim3(L.tab.nblk_line), dim3(32, L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py,
            pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart, C ? (const long long *)C->zq : nullptr,
            C ? (const int *)C->ze : nullptr, C ? C->tab.inst : nullptr, L.inst[0]);
@@ -764,7 +773,8 @@ static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, in
   const Inst *tabc = rc ? h->lv[l + 1].tab.inst : nullptr;
   switch (L.tab.nch2) {
 #define HPCG_BFP_CASE(N) \
-  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, dpart, prolong, s); break;
+  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, dpart, prolong, s, h->opt.bfp_split != 0); \
+    break;
     HPCG_BFP_CASE(1) HPCG_BFP_CASE(2) HPCG_BFP_CASE(3) HPCG_BFP_CASE(4) HPCG_BFP_CASE(5) HPCG_BFP_CASE(6)
 #undef HPCG_BFP_CASE
     default: return HPCG_ERR_UNSUPPORTED;
@@ -1444,6 +1454,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->block_fp = 1;
   opt->cluster_tail = 0;
   opt->restart_every = 0;
+  opt->bfp_split = 0;
   return HPCG_OK;
 }
 

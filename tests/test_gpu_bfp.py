@@ -126,3 +126,41 @@ def test_cluster_tail_with_kappa_matches_oracle():
     o = OracleProblem(*dims, levels=4, kappa=kappa)
     r = normal(n, 40)
     assert normwise(host(g.mg_vcycle(dev(r))), o.mg(r)) <= TOL64
+
+
+SPLIT_CASES = [((96, 64, 80), 4), ((192, 32, 48), 4), ((256, 16, 32), 3), ((128, 40, 24), 4)]
+
+
+@pytest.mark.parametrize("dims,levels", SPLIT_CASES)
+@pytest.mark.parametrize("with_kappa", [False, True])
+def test_split_lines_give_the_same_vcycle_bits(dims, levels, with_kappa):
+    """hpcg_options.bfp_split: lines of 2-4 chunks with one warp per chunk give
+    the V-cycle of one warp per line bit for bit, for any launch shape."""
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    n = int(np.prod(dims))
+    kappa = dev(uniform(n, 0.0, 1.0, 42)) if with_kappa else None
+    g1 = HpcgProblem(*dims, levels=levels, kappa=kappa)
+    gs = HpcgProblem(*dims, levels=levels, kappa=kappa, bfp_split=True)
+    r = dev(normal(n, 43))
+    z1 = host(g1.mg_vcycle(r))
+    np.testing.assert_array_equal(host(gs.mg_vcycle(r)), z1)
+    for lpc, zc in [(1, 1), (8, 4), (2, 3)]:
+        gs.set_launch_shapes([[1, 1, lpc, zc]] * levels)
+        np.testing.assert_array_equal(host(gs.mg_vcycle(r)), z1)
+
+
+@pytest.mark.parametrize("dims,levels", SPLIT_CASES[:2])
+def test_split_lines_cg_matches_oracle(dims, levels):
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    n = int(np.prod(dims))
+    gs = HpcgProblem(*dims, levels=levels, bfp_split=True)
+    o = OracleProblem(*dims, levels=levels)
+    b = normal(n, 44)
+    x, st = gs.pcg_solve(dev(b), max_iters=30, tol=0.0)
+    xo, ho = o.pcg(b, max_iters=30, tol=0.0)
+    h = np.asarray(st.history)
+    live = ho > 1e-11
+    assert np.max(np.abs(h[live] - ho[live]) / ho[live]) <= 1e-6
+    assert normwise(host(x), xo) <= 1e-10
