@@ -15,11 +15,12 @@ def lib_path():
     return os.path.join(_OUT_DIR, "libhpcg_oracle.so")
 
 
-def compile_source(src, out):
-    """Compiles an oracle source file (no FMA contraction, one thread) to a shared library."""
+def compile_source(src, out, extra=()):
+    """Compiles an oracle source file (no FMA contraction, one thread) to a shared library;
+    extra: more compiler flags (the sanitizer test's instrumentation)."""
     tmp = out + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, src, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"] + list(extra) + [
+        "-o", tmp, src, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, out)
     return out
