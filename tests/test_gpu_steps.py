@@ -179,3 +179,36 @@ def test_results_independent_of_launch_shape(precision):
     xb, sb = gb.pcg_solve(b, max_iters=12, tol=0.0)
     np.testing.assert_array_equal(np.asarray(sa.history), np.asarray(sb.history))
     np.testing.assert_array_equal(host(xa), host(xb))
+
+
+def _random_grids(count, seed):
+    """Grids with 1-4 levels, each dimension m 2^(levels-1) with m in 1..9 and at
+    least 2 points on the coarsest level (odd coarsest dimensions, dimensions of
+    2, x-lines from 2 to 144 points), at most 40,000 rows."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        levels = int(rng.integers(1, 5))
+        f = 1 << (levels - 1)
+        dims = tuple(int(rng.integers(2 if f == 1 else 1, 10)) * f for _ in range(3))
+        if min(d // f for d in dims) < 2 or np.prod(dims) > 40000:
+            continue
+        out.append((dims, levels))
+    return out
+
+
+@pytest.mark.parametrize("dims,levels", _random_grids(12, 2024))
+def test_random_grids_against_oracle(dims, levels):
+    """Seeded random grids: setup maps bit-exact; SpMV, one smoother
+    application and the V-cycle within 1e-12 of the oracle on every level."""
+    g, o = _pair(dims, levels)
+    for l in range(levels):
+        np.testing.assert_array_equal(host(g.get_colors(l)), o.colors(l))
+        n = o.n(l)
+        x, r, z0 = normal(n, 81 + l), normal(n, 82 + l), normal(n, 83 + l)
+        assert normwise(host(g.spmv(dev(x), l)), o.spmv(x, l)) <= TOL64
+        assert normwise(host(g.rbgs(dev(r), dev(z0), l)), o.rbgs(r, z0, l)) <= TOL64
+        if l < levels - 1:
+            np.testing.assert_array_equal(host(g.get_f2c(l)), o.f2c(l))
+    r = normal(o.n(0), 84)
+    assert normwise(host(g.mg_vcycle(dev(r))), o.mg(r)) <= TOL64
