@@ -487,18 +487,20 @@ def run_gpu(args):
     barrier()
     torch.cuda.synchronize()
     l0 = launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    # an event after every step: the mean over the K steps is the value, the
+    # per-step times give the spread (the paper averages 10 repetitions)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
         step()
-    e1.record(stream)
+        evs[i + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     launches = launch_count() - l0
-    ms = e0.elapsed_time(e1) / args.steps
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    ms = evs[0].elapsed_time(evs[-1]) / args.steps
     clocks = sampler.stop()
-    ms = max_over_ranks([ms], world, dev)[0]
+    ms, ms_min = max_over_ranks([ms, min(step_ms)], world, dev)
 
     flops_iter = hpcg_flops_per_iter(NX, NY, NZ, LEVELS)
     value = whole_job_gflops(world, flops_iter * ITERS, ms)
@@ -700,7 +702,8 @@ def run_gpu(args):
     line = {
         "metric": "HPCG-rule GFLOP/s at 192^3 (FP64 MG-PCG); mixed vs FP64 time to 1e-9",
         "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "ms_per_step": ms, "ms_per_step_min": ms_min, "ms_per_step_spread": [min(step_ms), max(step_ms)],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (HPCG generates its own operator; b = A*ones)",
         "config": {"workload": "FP64 MG-PCG 192^3, 4 levels (192/96/48/24), 1 pre + 1 post symmetric RBGS, "
                                "50 CG iterations per step, b=A*ones, x0=0",
@@ -732,7 +735,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
