@@ -6,7 +6,7 @@ import torch
 
 from hpcg_inputs import normal, uniform
 from oracle import OracleProblem
-from tests.gpu_util import TOL64, dev, host, need_gpu, normwise
+from tests.gpu_util import TOL32, TOL64, dev, host, need_gpu, normwise
 
 pytestmark = pytest.mark.gpu
 
@@ -212,3 +212,15 @@ def test_random_grids_against_oracle(dims, levels):
             np.testing.assert_array_equal(host(g.get_f2c(l)), o.f2c(l))
     r = normal(o.n(0), 84)
     assert normwise(host(g.mg_vcycle(dev(r))), o.mg(r)) <= TOL64
+
+
+@pytest.mark.parametrize("dims,levels", _random_grids(6, 2025))
+def test_random_grids_mixed_vcycle(dims, levels):
+    """The FP32 preconditioner on seeded random grids, within the FP32
+    tolerance of the oracle's FP64 V-cycle."""
+    from paper_2304_08232_gb300 import HpcgProblem
+    need_gpu()
+    g = HpcgProblem(*dims, levels=levels, precision="mixed")
+    o = OracleProblem(*dims, levels=levels)
+    r = normal(o.n(0), 85)
+    assert normwise(host(g.mg_vcycle(dev(r))), o.mg(r)) <= TOL32
