@@ -644,10 +644,21 @@ def run_gpu(args):
     mixed_l0_ms = breakdown["mixed"]["smoother_ms"][0]
     mixed_l0_bytes = 74.5 * n  # FP32 analogue of the 158 n above: runs of 2, 3, 4, 5, 6, 6, 6 n (+ 0.5 n restricted
     #                            residual) before the coarse correction, 7 x 6 n after it (refinement is its own kernel)
+    # the binding roofline of one FP64 iteration, both terms: bytes over the
+    # copy bandwidth, and executed FP64 instructions (fixed-point sums leave 6
+    # FMA per finest-level row: p and x updates, r update and r.r, p.Ap, r.z)
+    # over the FP64 pipe (2 per SM per clock, 152 SMs)
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    bytes_us = algorithmic_bytes_per_iter(NX, NY, NZ, LEVELS) / (hbm_peak * 1e9) * 1e6
+    fp64_us = 6 * n / (2 * 152 * sm_mhz * 1e6) * 1e6
     by_form = {
         "fp64_192^3_50_iters": {
             "dominant_kernel": roofline["kernel"], "dominant_kernel_frac": roofline["frac"],
-            "whole_solve_roofline": whole_solve_roofline(algorithmic_bytes_per_iter(NX, NY, NZ, LEVELS) * ITERS, ms, hbm_peak)},
+            "whole_solve_roofline": whole_solve_roofline(algorithmic_bytes_per_iter(NX, NY, NZ, LEVELS) * ITERS, ms, hbm_peak),
+            "binding_roofline_per_iter": {"bytes_term_us": bytes_us, "fp64_term_us": fp64_us,
+                                          "bound": "hbm" if bytes_us >= fp64_us else "fp64",
+                                          "measured_us": ms * 1e3 / ITERS,
+                                          "frac": max(bytes_us, fp64_us) / (ms * 1e3 / ITERS)}},
         "mixed_192^3_to_1e-9": {
             "dominant_kernel": "k_gs_lines<float,3,PAIR> (finest level, FP32 colour-pair runs)",
             "dominant_kernel_bytes_per_vcycle": mixed_l0_bytes, "dominant_kernel_ms_per_vcycle": mixed_l0_ms,
