@@ -112,6 +112,7 @@ __device__ __forceinline__ void fin_apply(CgState &c, double s, double *hist) {
       c.first = 1;
       c.restart = 0;
       c.restarts += 1;
+      c.xpend = 0;  // applied before the residual was replaced (k_update_x_restart)
     }
     if (c.first) {
       c.beta = 0.0;
