@@ -179,6 +179,50 @@ int hpcg_prolong_add(hpcg_handle h, int level, const double *zc_dev, double *z_d
  * precision; FP64 [n_0] in and out; r and z must not overlap. */
 int hpcg_mg_vcycle(hpcg_handle h, const double *r_dev, double *z_dev, void *stream);
 
+/* --- the V-cycle stage by stage, and its level vectors ------------------------ */
+/* Listing 1 on level l is: z_l <- 0 and pre-smoothing; on a non-coarsest level
+ * the residual restricted by injection into the next level's right-hand side,
+ * r_{l+1} <- R (r_l - A_l z_l) (Section II-F); the recursion; then z_l <- z_l +
+ * R^T z_{l+1} (refinement and correction) and post-smoothing.  These calls run
+ * one such stage on one level with the launches hpcg_mg_vcycle itself issues
+ * for it (restriction and refinement fused into smoother runs where the
+ * V-cycle fuses them; the coarse end's single-launch kernel when
+ * hpcg_options.cluster_tail or .persistent put the level there), on the level
+ * vectors the handle keeps, so that running PRE on levels 0..L-1 and then
+ * POST on levels L-2..0 reproduces hpcg_mg_vcycle bit for bit.  Their purpose
+ * is to observe and drive the coarse levels, whose effect on the V-cycle's
+ * output is otherwise hidden (with this smoother and injection the coarse
+ * correction lands on points that the post-smoother recomputes first).
+ *
+ * Stages (level < L-1 for REFINE and POST):
+ *   HPCG_STAGE_PRE:    z_l <- 0, pre-smoothing (one application on the coarsest
+ *                      level), and on a non-coarsest level r_{l+1} <- R (r_l - A_l z_l).
+ *   HPCG_STAGE_REFINE: z_l <- z_l + R^T z_{l+1} alone.
+ *   HPCG_STAGE_POST:   z_l <- z_l + R^T z_{l+1}, then post-smoothing.
+ * Level vectors: r_l and z_l for l >= 1 live in the handle's workspace; on
+ * level 0 r_0 is r0_dev (FP64 [n_0], caller's) and z_0 is z0_dev with block_fp
+ * off, else the workspace's (block floating point, or FP32 in mixed
+ * precision) with z0_dev receiving the FP64 result of POST (and of PRE when
+ * levels == 1).  r0_dev and z0_dev are required on level 0 (distinct; 16-byte
+ * aligned with block_fp) and ignored on other levels.  Errors: INVALID_ARG for
+ * a level or stage out of range or missing level-0 vectors. */
+typedef enum { HPCG_STAGE_PRE = 0, HPCG_STAGE_REFINE = 1, HPCG_STAGE_POST = 2 } hpcg_stage;
+int hpcg_mg_stage(hpcg_handle h, int level, int stage, const double *r0_dev, double *z0_dev, void *stream);
+
+/* Copies level `level`'s right-hand side r_l and iterate z_l, as the last
+ * V-cycle or stage on this handle left them, into caller device buffers of
+ * n_level FP64 values (either pointer may be NULL).  Block-floating-point z is
+ * converted exactly (each value is its mantissa times the line's power of
+ * two), FP32 vectors are widened.  Level 0: r_dev must be NULL (r_0 is the
+ * caller's), and z_0 exists only with block_fp or mixed precision
+ * (UNSUPPORTED otherwise). */
+int hpcg_get_level_vectors(hpcg_handle h, int level, double *r_dev, double *z_dev, void *stream);
+/* Writes r_l and/or z_l of `level` (same rules).  Block floating point stores
+ * each x-line at the largest exponent of its values, truncating every value
+ * to 58 bits below that line's largest power of two; mixed precision rounds
+ * to FP32.  hpcg_get_level_vectors returns the stored values. */
+int hpcg_set_level_vectors(hpcg_handle h, int level, const double *r_dev, const double *z_dev, void *stream);
+
 /* out_dev[0] = a . b over n FP64 values, deterministic fixed-order reduction. */
 int hpcg_dot(hpcg_handle h, long n, const double *a_dev, const double *b_dev, double *out_dev, void *stream);
 

@@ -46,6 +46,9 @@ SIGNATURES = {
     "hpcg_restrict_residual": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "hpcg_prolong_add": (_i, [_vp, _i, _vp, _vp, _vp]),
     "hpcg_mg_vcycle": (_i, [_vp, _vp, _vp, _vp]),
+    "hpcg_mg_stage": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "hpcg_get_level_vectors": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hpcg_set_level_vectors": (_i, [_vp, _i, _vp, _vp, _vp]),
     "hpcg_dot": (_i, [_vp, _l, _vp, _vp, _vp, _vp]),
     "hpcg_waxpby": (_i, [_vp, _l, _d, _vp, _d, _vp, _vp, _vp]),
     "hpcg_pcg_solve": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
@@ -89,6 +92,7 @@ SIGNATURES = {
 HPCG_OK = 0
 HPCG_ERR_NOT_CONVERGED = 4
 FP64, MIXED = 0, 1
+STAGE_PRE, STAGE_REFINE, STAGE_POST = 0, 1, 2
 
 _LIB = None
 

@@ -207,6 +207,33 @@ class HpcgProblem:
         check(self.lib.hpcg_mg_vcycle(self.h, _ptr(r), _ptr(out), _stream()), "hpcg_mg_vcycle")
         return out
 
+    # -- the V-cycle stage by stage (hpcg_mg_stage) and its level vectors ---------------
+    def mg_stage(self, level, stage, r0=None, z0=None):
+        """One stage ("pre", "refine" or "post") of Listing 1 on `level`, on the
+        handle's level vectors; level 0 takes r0 and z0 (FP64 [n_0])."""
+        code = {"pre": _lib.STAGE_PRE, "refine": _lib.STAGE_REFINE, "post": _lib.STAGE_POST}[stage]
+        if level == 0:
+            _need(r0, self.n, name="r0"), _need(z0, self.n, name="z0")
+        check(self.lib.hpcg_mg_stage(self.h, level, code, _ptr(r0) if level == 0 else None,
+                                     _ptr(z0) if level == 0 else None, _stream()), "hpcg_mg_stage")
+        return z0
+
+    def get_level_vectors(self, level, r=True, z=True):
+        """(r_l, z_l) as FP64 tensors (None where not asked for)."""
+        n = self.level_n(level)
+        rt = torch.empty(n, dtype=_f64, device=self.device) if r else None
+        zt = torch.empty(n, dtype=_f64, device=self.device) if z else None
+        check(self.lib.hpcg_get_level_vectors(self.h, level, _ptr(rt), _ptr(zt), _stream()), "hpcg_get_level_vectors")
+        return rt, zt
+
+    def set_level_vectors(self, level, r=None, z=None):
+        n = self.level_n(level)
+        if r is not None:
+            _need(r, n, name="r")
+        if z is not None:
+            _need(z, n, name="z")
+        check(self.lib.hpcg_set_level_vectors(self.h, level, _ptr(r), _ptr(z), _stream()), "hpcg_set_level_vectors")
+
     def dot(self, a, b):
         out = torch.empty(1, dtype=_f64, device=self.device)
         check(self.lib.hpcg_dot(self.h, a.numel(), _ptr(a), _ptr(b), _ptr(out), _stream()), "hpcg_dot")

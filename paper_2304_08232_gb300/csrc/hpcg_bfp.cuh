@@ -124,7 +124,9 @@ __device__ __forceinline__ long long bfp_new_value(long long t, int S, int sout,
 // load with L2-coherent loads (data written earlier in the same launch).
 // g1: the grid when count == 1 (a kernel parameter, so that a single grid's
 // launch does not wait for a table load before its first data loads).
-template <int NC, bool COH>
+// REFINE_ONLY: stop after the fused refinement and store the refined line
+// (hpcg_mg_stage's refinement stage; the V-cycle's kernels never set it).
+template <int NC, bool COH, bool REFINE_ONLY = false>
 __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__restrict__ tab, const Inst &g1, int count, int lpc, int zc,
                                              int py, int pz, int pa, int steps, int vmask, const double *__restrict__ r,
                                              long long *__restrict__ zq, int *__restrict__ ze, const double *__restrict__ invd,
@@ -206,6 +208,16 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
         qo[c] = shr_q(qo[c], Sp - eo);
       }
       eo = (eo > kFxMaxE || e_c > kFxMaxE) ? kBfpNaN : Sp;
+      if constexpr (REFINE_ONLY) {  // store the refined line at its exponent
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int xe = 64 * c + 2 * lane;
+          if (xe < nx)
+            *reinterpret_cast<longlong2 *>(qg + rowbase + xe) = eo == kBfpNaN ? make_longlong2(0, 0) : make_longlong2(qe[c], qo[c]);
+        }
+        if (lane == 0) eg[li] = eo;
+        continue;  // the plane sums carried to the next plane are not needed without colour steps
+      }
     }
     double rE[NC], rO[NC];
     ld_pairs_d<NC, COH>(rg + rowbase, nx, lane, rE, rO);
@@ -374,6 +386,22 @@ __global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ t
                           zout, dpart, zqc, zec, tabcp);
 }
 
+// The refinement fused into a post-smoother's first run, alone: the same
+// block work as k_gs_lines_bfp (same launch shape and arguments), stopping
+// once the refined class (0,0) line is stored (hpcg_mg_stage).
+template <int NC>
+__global__ void __launch_bounds__(256) k_gs_lines_bfp_refine(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
+                                                             int steps, int vmask, const double *__restrict__ r, long long *__restrict__ zq,
+                                                             int *__restrict__ ze, const double *__restrict__ invd,
+                                                             const CgState *__restrict__ st, const Inst *__restrict__ tabc,
+                                                             double *__restrict__ rc, const double *__restrict__ kap, double *__restrict__ zout,
+                                                             double *__restrict__ dpart, const long long *__restrict__ zqc,
+                                                             const int *__restrict__ zec, const Inst *__restrict__ tabcp, const Inst g1) {
+  pdl_enter();
+  gs_bfp_block<NC, false, true>(blockIdx.x, threadIdx.y, tab, g1, count, lpc, zc, py, pz, pa, steps, vmask, r, zq, ze, invd, st, tabc, rc,
+                                kap, zout, dpart, zqc, zec, tabcp);
+}
+
 // ---------------------------------------------------------------------------
 // The same colour-pair runs with each x-line split over W warps, one 64-point
 // chunk each (x in [64k, 64k + 64), the lane holding the pair x = 64k + 2 lane,
@@ -493,6 +521,12 @@ __global__ void __launch_bounds__(1024)
       qe = shr_q(qe, Sp - eo) + shr_q(cv, Sp - e_c);
       qo = shr_q(qo, Sp - eo);
       eo = (eo > kFxMaxE || e_c > kFxMaxE) ? kBfpNaN : Sp;
+    }
+    if (steps == 0) {  // refinement alone (hpcg_mg_stage), the same for every warp of the block: no barrier is skipped unevenly
+      if (zqc && xin)
+        *reinterpret_cast<longlong2 *>(qg + rowbase + xe) = eo == kBfpNaN ? make_longlong2(0, 0) : make_longlong2(qe, qo);
+      if (zqc && lok && k == 0 && lane == 0) eg[li] = eo;
+      continue;
     }
     double rE = 0.0, rO = 0.0;
     if (xin) {
@@ -735,20 +769,78 @@ __device__ __forceinline__ void bfp_tail_runs(const BfpTailPlan &P, int l, const
   }
 }
 
+// Refinement of level l from level l+1 over every line of the coarse level.
+__device__ __forceinline__ void bfp_tail_refine(const BfpTailPlan &P, int l, const CgState *st) {
+  const BfpTailLevel &F = P.lv[l], &C = P.lv[l + 1];
+  const int nw = gridDim.x * blockDim.y;
+  for (int wl = blockIdx.x * blockDim.y + threadIdx.y; wl < C.nlines; wl += nw)
+    prolong_bfp_line<true>(wl, threadIdx.x, F.tab, C.tab, P.count, C.zq, C.ze, F.zq, F.ze, st);
+}
+
+// stage_level < 0: the whole coarse end (levels first..last down, then back
+// up to first).  Otherwise only stage `stage` (HPCG_STAGE_PRE / _REFINE /
+// _POST of hpcg_mg_stage) of level stage_level, with the same arithmetic.
 template <int NC>
 __global__ void __launch_bounds__(32 * kBfpTailWarps) k_vcycle_tail_bfp(const BfpTailPlan *__restrict__ plan,
-                                                                         const CgState *__restrict__ st) {
+                                                                         const CgState *__restrict__ st, int stage_level, int stage) {
   pdl_enter();
   const BfpTailPlan &P = *plan;
+  if (stage_level >= 0) {
+    const int l = stage_level;
+    if (stage == HPCG_STAGE_PRE) {
+      bfp_tail_runs<NC>(P, l, P.lv[l].pre, P.lv[l].npre, true, l < P.last, st);
+    } else {
+      bfp_tail_refine(P, l, st);
+      if (stage == HPCG_STAGE_POST) {
+        cluster_barrier();
+        bfp_tail_runs<NC>(P, l, P.lv[l].post, P.lv[l].npost, false, false, st);
+      }
+    }
+    return;
+  }
   for (int l = P.first; l <= P.last; ++l) bfp_tail_runs<NC>(P, l, P.lv[l].pre, P.lv[l].npre, true, l < P.last, st);
   for (int l = P.last - 1; l >= P.first; --l) {
-    const BfpTailLevel &F = P.lv[l], &C = P.lv[l + 1];
-    const int nw = gridDim.x * blockDim.y;
-    for (int wl = blockIdx.x * blockDim.y + threadIdx.y; wl < C.nlines; wl += nw)
-      prolong_bfp_line<true>(wl, threadIdx.x, F.tab, C.tab, P.count, C.zq, C.ze, F.zq, F.ze, st);
+    bfp_tail_refine(P, l, st);
     cluster_barrier();
-    bfp_tail_runs<NC>(P, l, F.post, F.npost, false, false, st);
+    bfp_tail_runs<NC>(P, l, P.lv[l].post, P.lv[l].npost, false, false, st);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Level vectors into and out of block floating point, for inspection and for
+// stage-by-stage checks of the V-cycle (hpcg_get_level_vectors,
+// hpcg_set_level_vectors).  One warp per x-line of every instance of a level
+// (`nlines` lines in all, numbered as the exponents are).
+
+__global__ void __launch_bounds__(256) k_bfp_to_double(const Inst *__restrict__ tab, int count, long nlines, const long long *__restrict__ zq,
+                                                       const int *__restrict__ ze, double *__restrict__ out) {
+  const long wl = (long)blockIdx.x * blockDim.y + threadIdx.y;
+  if (wl >= nlines) return;
+  const int ii = count == 1 ? 0 : find_inst<5>(tab, count, (int)wl);
+  const Inst g = tab[ii];
+  const long base = g.off + (wl - g.poff) * g.nx;  // row of x = 0 on line (y, z): x + nx (y + ny z)
+  const int e = ze[wl];
+  for (int x = threadIdx.x; x < g.nx; x += 32) out[base + x] = e == kBfpNaN ? bfp_nan() : fx_to_double(zq[base + x], e);
+}
+
+// Each line gets the largest biased exponent of its values (at least
+// kFxMinE) as its exponent and every value is truncated at that scale
+// (|q| < 2^58, the largest with bit 57 set, as the colour runs store lines);
+// a line holding a non-finite value or one beyond the range of the fixed-point
+// sums reads as NaN.
+__global__ void __launch_bounds__(256) k_bfp_from_double(const Inst *__restrict__ tab, int count, long nlines, const double *__restrict__ in,
+                                                         long long *__restrict__ zq, int *__restrict__ ze) {
+  const long wl = (long)blockIdx.x * blockDim.y + threadIdx.y;
+  if (wl >= nlines) return;
+  const int ii = count == 1 ? 0 : find_inst<5>(tab, count, (int)wl);
+  const Inst g = tab[ii];
+  const long base = g.off + (wl - g.poff) * g.nx;
+  int emax = kFxMinE;
+  for (int x = threadIdx.x; x < g.nx; x += 32) emax = max(emax, fx_exp(in[base + x]));
+  emax = warp_max(emax);
+  const bool bad = emax > kFxMaxE;  // includes Inf and NaN (biased exponent 2047)
+  for (int x = threadIdx.x; x < g.nx; x += 32) zq[base + x] = bad ? 0LL : fx_of(in[base + x], emax);
+  if (threadIdx.x == 0) ze[wl] = bad ? kBfpNaN : emax;
 }
 
 }  // namespace hpcg

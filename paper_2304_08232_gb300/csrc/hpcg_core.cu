@@ -525,8 +525,9 @@ static int build_fp64_tail(hpcg_ctx *h) {
 }
 
 // Launches the tail for precision T (0: FP64 plan, 1: FP32 plan) as a cooperative kernel.
+// stage_level >= 0: only that stage of that level (hpcg_mg_stage).
 template <typename T>
-static int enqueue_tail(hpcg_ctx *h, cudaStream_t s, const CgState *st) {
+static int enqueue_tail(hpcg_ctx *h, cudaStream_t s, const CgState *st, int stage_level = -1, int stage = 0) {
   unsigned *bar = (unsigned *)(h->ws + h->o_sync);
   int *err = (int *)(bar + 2);
   const TailPlan *plan = (const TailPlan *)(h->ws + h->o_tail + (sizeof(T) == 4 ? sizeof(TailPlan) : 0));
@@ -541,7 +542,7 @@ static int enqueue_tail(hpcg_ctx *h, cudaStream_t s, const CgState *st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<T>, plan, bar, err, h->wait_limit, const_cast<CgState *>(st));
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<T>, plan, bar, err, h->wait_limit, const_cast<CgState *>(st), stage_level, stage);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (e != cudaSuccess) return cuda_fail(e, "k_vcycle_tail (cooperative launch)");
   return HPCG_OK;
@@ -747,15 +748,22 @@ static int enqueue_prolong(hpcg_ctx *h, int l, const T *zc, T *z, cudaStream_t s
 template <int NC>
 static void launch_gs_bfp(const LevelData &L, int count, int py, int pz, int pa, int steps, int vmask, const double *r, const double *invd,
                           const CgState *st, const Inst *tabc, double *rc, const double *kap, double *zout, double *dpart,
-                          const LevelData *C, cudaStream_t s, bool split) {
+                          const LevelData *C, cudaStream_t s, bool split, bool refine_only) {
   if constexpr (NC >= 2 && NC <= 4) {
-    // lines of 2-4 chunks: one warp per 64-point chunk (k_gs_lines_bfp_split)
+    // lines of 2-4 chunks: one warp per 64-point chunk (k_gs_lines_bfp_split;
+    // steps == 0 there is the refinement alone)
     if (split && L.tab.line_lpc <= kBfpSplitMaxLines) {
       launch_k(k_gs_lines_bfp_split<NC>, dim3(L.tab.nblk_line), dim3(32, NC * L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc,
                L.tab.line_zc, py, pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart,
                C ? (const long long *)C->zq : nullptr, C ? (const int *)C->ze : nullptr, C ? C->tab.inst : nullptr, L.inst[0]);
       return;
     }
+  }
+  if (refine_only) {  // hpcg_mg_stage: the fused refinement alone
+    launch_k(k_gs_lines_bfp_refine<NC>, dim3(L.tab.nblk_line), dim3(32, L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc,
+             L.tab.line_zc, py, pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart,
+             C ? (const long long *)C->zq : nullptr, C ? (const int *)C->ze : nullptr, C ? C->tab.inst : nullptr, L.inst[0]);
+    return;
   }
   launch_k(k_gs_lines_bfp<NC>, dim3(L.tab.nblk_line), dim3(32, L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc, L.tab.line_zc, py,
            pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart, C ? (const long long *)C->zq : nullptr,
@@ -773,7 +781,8 @@ static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, in
   const Inst *tabc = rc ? h->lv[l + 1].tab.inst : nullptr;
   switch (L.tab.nch2) {
 #define HPCG_BFP_CASE(N) \
-  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, dpart, prolong, s, h->opt.bfp_split != 0); \
+  case N: launch_gs_bfp<N>(L, h->count, py, pz, pa, steps, vmask, r, invd, st, tabc, rc, kap, zout, dpart, prolong, s, h->opt.bfp_split != 0, \
+                           steps == 0); \
     break;
     HPCG_BFP_CASE(1) HPCG_BFP_CASE(2) HPCG_BFP_CASE(3) HPCG_BFP_CASE(4) HPCG_BFP_CASE(5) HPCG_BFP_CASE(6)
 #undef HPCG_BFP_CASE
@@ -821,7 +830,7 @@ static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps,
 
 
 // Levels bfp_tail_first..L-1 of the V-cycle in one cluster launch.
-static int enqueue_tail_bfp(hpcg_ctx *h, cudaStream_t s, const CgState *st) {
+static int enqueue_tail_bfp(hpcg_ctx *h, cudaStream_t s, const CgState *st, int stage_level = -1, int stage = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kBfpTailCtas);
   cfg.blockDim = dim3(32, kBfpTailWarps);
@@ -833,7 +842,7 @@ static int enqueue_tail_bfp(hpcg_ctx *h, cudaStream_t s, const CgState *st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_vcycle_tail_bfp<1>, (const BfpTailPlan *)(h->ws + h->o_tail_bfp), st);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_vcycle_tail_bfp<1>, (const BfpTailPlan *)(h->ws + h->o_tail_bfp), st, stage_level, stage);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (e != cudaSuccess) return cuda_fail(e, "k_vcycle_tail_bfp (cluster launch)");
   prof_mark(PK_TAIL, h->bfp_tail_first);
@@ -893,6 +902,115 @@ static int enqueue_vcycle_t(hpcg_ctx *h, T *const *rl, T *const *zl, cudaStream_
     TRY(enqueue_prolong<T>(h, l, zl[l + 1], zl[l], s, st));                     // z <- z + refine(z_c)
     TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], h->opt.post_sweeps, s, st));    // post-smoothing
   }
+  return HPCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One stage of Listing 1 on one level (hpcg_mg_stage): exactly the launches
+// the V-cycle above issues for that stage, on the handle's level vectors, so
+// that the stages run in V-cycle order reproduce hpcg_mg_vcycle bit for bit.
+enum VStore { VS_BFP = 0, VS_F64 = 1, VS_F32 = 2 };
+static int vstore_of(const hpcg_ctx *h) {
+  if (h->opt.precision == HPCG_MIXED) return VS_F32;
+  return h->use_bfp ? VS_BFP : VS_F64;
+}
+
+template <typename T>
+static int enqueue_stage_t(hpcg_ctx *h, int l, int stage, T *const *rl, T *const *zl, cudaStream_t s) {
+  const bool coarsest = l == h->levels - 1;
+  if (h->tail_first > 0 && l >= h->tail_first) return enqueue_tail<T>(h, s, nullptr, l, stage);
+  if (stage == HPCG_STAGE_PRE) {
+    bool fused = false;
+    TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], coarsest ? 1 : h->opt.pre_sweeps, s, nullptr, true, coarsest ? nullptr : rl[l + 1],
+                            &fused));
+    if (!coarsest && !fused) TRY(enqueue_restrict<T>(h, l, rl[l], zl[l], rl[l + 1], s, nullptr));
+    return HPCG_OK;
+  }
+  TRY(enqueue_prolong<T>(h, l, zl[l + 1], zl[l], s, nullptr));
+  if (stage == HPCG_STAGE_POST) TRY(enqueue_smoother<T>(h, l, rl[l], zl[l], h->opt.post_sweeps, s, nullptr));
+  return HPCG_OK;
+}
+
+static int enqueue_stage(hpcg_ctx *h, int l, int stage, const double *r0, double *z0, cudaStream_t s) {
+  const bool coarsest = l == h->levels - 1;
+  const int vs = vstore_of(h);
+  if (vs == VS_BFP) {
+    if (h->bfp_tail_first > 0 && l >= h->bfp_tail_first) return enqueue_tail_bfp(h, s, nullptr, l, stage);
+    const double *r = l == 0 ? r0 : h->lv[l].r;
+    if (stage == HPCG_STAGE_PRE)
+      return enqueue_smoother_bfp(h, l, r, coarsest ? 1 : h->opt.pre_sweeps, s, nullptr, true, coarsest ? nullptr : h->lv[l + 1].r,
+                                  (coarsest && l == 0) ? z0 : nullptr);
+    if (stage == HPCG_STAGE_REFINE)  // the refinement of the post-smoother's first run (class (0,0)), without its colour steps
+      return enqueue_line_steps_bfp(h, l, 0, 0, 0, 0, r, s, nullptr, 0xF, nullptr, nullptr, nullptr, &h->lv[l + 1]);
+    return enqueue_smoother_bfp(h, l, r, h->opt.post_sweeps, s, nullptr, false, nullptr, l == 0 ? z0 : nullptr, nullptr, true);
+  }
+  if (vs == VS_F64) {
+    double *rl[kMaxLevels], *zl[kMaxLevels];
+    rl[0] = const_cast<double *>(r0);
+    zl[0] = z0;
+    for (int k = 1; k < h->levels; ++k) {
+      rl[k] = h->lv[k].r;
+      zl[k] = h->lv[k].z;
+    }
+    return enqueue_stage_t<double>(h, l, stage, rl, zl, s);
+  }
+  float *rl[kMaxLevels], *zl[kMaxLevels];
+  for (int k = 0; k < h->levels; ++k) {
+    rl[k] = h->lv[k].r32;
+    zl[k] = h->lv[k].z32;
+  }
+  const LevelData &L0 = h->lv[0];
+  if (l == 0 && stage != HPCG_STAGE_REFINE) {  // the FP32 copy of r, as the V-cycle makes it
+    launch_k(k_convert<double, float>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, r0, L0.r32, (const CgState *)nullptr);
+    CKL("k_convert");
+  }
+  TRY(enqueue_stage_t<float>(h, l, stage, rl, zl, s));
+  if (l == 0 && stage == HPCG_STAGE_POST) {
+    launch_k(k_convert<float, double>, L0.tab.nblk_red, kRedThreads, 0, s, L0.tab.inst, h->count, L0.z32, z0, (const CgState *)nullptr);
+    CKL("k_convert");
+  }
+  return HPCG_OK;
+}
+
+// Level vectors between the caller's FP64 buffers and the handle's storage
+// (to_user: storage -> v).  which: 0 = r, 1 = z.
+static int copy_level_vector(hpcg_ctx *h, int l, int which, double *v, bool to_user, cudaStream_t s) {
+  LevelData &L = h->lv[l];
+  const int vs = vstore_of(h);
+  if (vs == VS_F32) {
+    float *f = which == 0 ? L.r32 : L.z32;
+    if (to_user)
+      launch_k(k_convert<float, double>, L.tab.nblk_red, kRedThreads, 0, s, L.tab.inst, h->count, (const float *)f, v,
+               (const CgState *)nullptr);
+    else
+      launch_k(k_convert<double, float>, L.tab.nblk_red, kRedThreads, 0, s, L.tab.inst, h->count, (const double *)v, f,
+               (const CgState *)nullptr);
+    CKL("k_convert");
+    return HPCG_OK;
+  }
+  if (which == 1 && vs == VS_BFP) {
+    const dim3 grid((unsigned)((L.nlines + 7) / 8)), block(32, 8);
+    if (to_user)
+      launch_k(k_bfp_to_double, grid, block, 0, s, L.tab.inst, h->count, L.nlines, (const long long *)L.zq, (const int *)L.ze, v);
+    else
+      launch_k(k_bfp_from_double, grid, block, 0, s, L.tab.inst, h->count, L.nlines, (const double *)v, L.zq, L.ze);
+    CKL("k_bfp_convert");
+    return HPCG_OK;
+  }
+  double *d = which == 0 ? L.r : L.z;
+  if (to_user)
+    CK(cudaMemcpyAsync(v, d, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemcpyAsync(d, v, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+  return HPCG_OK;
+}
+
+static int level_vectors(hpcg_ctx *h, int level, double *r_dev, double *z_dev, bool to_user, cudaStream_t s) {
+  if (level == 0 && r_dev) return HPCG_ERR_INVALID_ARG;                      // the finest r is the caller's own
+  if (level == 0 && z_dev && vstore_of(h) == VS_F64) return HPCG_ERR_UNSUPPORTED;  // the finest z is the caller's z
+  TRY(ensure_ready(h, s));
+  if (r_dev) TRY(copy_level_vector(h, level, 0, r_dev, to_user, s));
+  if (z_dev) TRY(copy_level_vector(h, level, 1, z_dev, to_user, s));
   return HPCG_OK;
 }
 
@@ -1647,6 +1765,32 @@ int hpcg_mg_vcycle(hpcg_handle h, const double *r_dev, double *z_dev, void *stre
   TRY(ensure_ready(h, s));
   TRY(reset_error_word(h, s));
   return enqueue_vcycle(h, r_dev, z_dev, s, nullptr);
+}
+
+int hpcg_mg_stage(hpcg_handle h, int level, int stage, const double *r0_dev, double *z0_dev, void *stream) {
+  if (!h || level < 0 || level >= h->levels) return HPCG_ERR_INVALID_ARG;
+  if (stage != HPCG_STAGE_PRE && stage != HPCG_STAGE_REFINE && stage != HPCG_STAGE_POST) return HPCG_ERR_INVALID_ARG;
+  if (stage != HPCG_STAGE_PRE && level == h->levels - 1) return HPCG_ERR_INVALID_ARG;  // the coarsest level has no coarser one
+  if (level == 0 && (!r0_dev || !z0_dev || (const void *)r0_dev == (const void *)z0_dev)) return HPCG_ERR_INVALID_ARG;
+  if (level == 0 && vstore_of(h) == VS_BFP && ((reinterpret_cast<uintptr_t>(r0_dev) | reinterpret_cast<uintptr_t>(z0_dev)) & 15) != 0)
+    return HPCG_ERR_INVALID_ARG;  // hpcg_mg_vcycle would take the FP64-storage path for these
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(ensure_ready(h, s));
+  TRY(reset_error_word(h, s));
+  return enqueue_stage(h, level, stage, r0_dev, z0_dev, s);
+}
+
+int hpcg_get_level_vectors(hpcg_handle h, int level, double *r_dev, double *z_dev, void *stream) {
+  if (!h || level < 0 || level >= h->levels || (r_dev && r_dev == z_dev)) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  return level_vectors(h, level, r_dev, z_dev, true, (cudaStream_t)stream);
+}
+
+int hpcg_set_level_vectors(hpcg_handle h, int level, const double *r_dev, const double *z_dev, void *stream) {
+  if (!h || level < 0 || level >= h->levels || (r_dev && r_dev == z_dev)) return HPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  return level_vectors(h, level, const_cast<double *>(r_dev), const_cast<double *>(z_dev), false, (cudaStream_t)stream);
 }
 
 int hpcg_dot(hpcg_handle h, long n, const double *a_dev, const double *b_dev, double *out_dev, void *stream) {

@@ -159,11 +159,29 @@ __device__ __forceinline__ void tail_restrict(const TailPlan &P, int l, const Cg
   }
 }
 
+// stage_level < 0: the whole coarse end (levels first..last down, then back
+// up to first).  Otherwise only stage `stage` (HPCG_STAGE_PRE / _REFINE /
+// _POST of hpcg_mg_stage) of level stage_level, with the same arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(32 * kTailThreadsY) k_vcycle_tail(const TailPlan *__restrict__ plan, unsigned *bar, int *err,
-                                                                     long long limit, CgState *st) {
+                                                                     long long limit, CgState *st, int stage_level, int stage) {
   const TailPlan &P = *plan;
   unsigned target = 0;
+  if (stage_level >= 0) {
+    const int l = stage_level;
+    const TailLevel &L = P.lv[l];
+    if (stage == HPCG_STAGE_PRE) {
+      if (!tail_runs<T>(P, l, L.pre, L.npre, true, L.fuse != 0 && l < P.last, bar, target, err, limit, st)) return;
+      if (l < P.last && !L.fuse) tail_restrict<T>(P, l, st);
+    } else {
+      tail_prolong<T>(P, l, st);
+      if (stage == HPCG_STAGE_POST) {
+        if (!tail_barrier(bar, target, err, limit, st, P.count)) return;
+        tail_runs<T>(P, l, L.post, L.npost, false, false, bar, target, err, limit, st);
+      }
+    }
+    return;
+  }
   for (int l = P.first; l <= P.last; ++l) {
     const TailLevel &L = P.lv[l];
     if (!tail_runs<T>(P, l, L.pre, L.npre, true, L.fuse != 0 && l < P.last, bar, target, err, limit, st)) return;
