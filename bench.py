@@ -32,6 +32,22 @@ LEVELS = 4
 ITERS = 50
 HBM_FALLBACK_GBS = 6800.0
 L2_BYTES = 135528448
+# the metric both arms report (the GPU solve, and --impl reference: the CPU oracle)
+METRIC = "HPCG-rule GFLOP/s + HBM GB/s at 192^3; mixed vs FP64 time to 1e-9 residual"
+# FP64-pipe warp instructions of one FP64 CG iteration per finest-level row, from
+# one ncu capture of an iteration's kernels (sm__inst_executed_pipe_fp64.sum,
+# profiles/fp64_instructions_per_iteration.md); every level's work scales
+# with the finest level's rows.
+FP64_WARP_INSTR_PER_ROW_ITER = 0.3495
+
+
+def bench_config(world=1):
+    """The workload, the same for both arms."""
+    return {"workload": "FP64 MG-PCG %dx%dx%d, %d levels, 1 pre + 1 post symmetric RBGS, %d CG iterations per step, "
+                        "b=A*ones, x0=0" % (NX, NY, NZ, LEVELS, ITERS),
+            "grid": [NX, NY, NZ], "levels": LEVELS, "cg_iters_per_step": ITERS,
+            "l2": "working set (6 level-0 vectors = 340 MB) exceeds L2 (135.5 MB); no flush",
+            "parallelism": "replicas" if world > 1 else "1 GPU"}
 
 
 def level_sizes(nx, ny, nz, levels):
@@ -199,6 +215,24 @@ def time_breakdown(prob, b):
     return r
 
 
+def fp64_probe(dev):
+    """FP64 FMA issue rate of this GPU (hpcg_probe_fp64_rate: 8 blocks of 256
+    threads per SM, 8 independent FMA chains per thread)."""
+    import ctypes
+    import torch
+    from paper_2304_08232_gb300 import _lib
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = 8 * sms, 2000
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    ms, fma = ctypes.c_double(), ctypes.c_double()
+    rc = _lib.load().hpcg_probe_fp64_rate(blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ms), ctypes.byref(fma),
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise RuntimeError("hpcg_probe_fp64_rate failed: %d" % rc)
+    lanes = fma.value / (ms.value * 1e-3)
+    return {"sms": sms, "ms": ms.value, "lane_fma_per_s": lanes, "warp_instr_per_s": lanes / 32, "tflops": 2 * lanes / 1e12}
+
+
 def persistent_first(prob):
     import ctypes
     from paper_2304_08232_gb300 import _lib
@@ -222,21 +256,40 @@ def tuned_shapes(prob):
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(steps_iters=2, nx=NX, ny=NY, nz=NZ):
-    """The CPU oracle (single thread, as it stands) on a bounded sample of the
-    workload: `steps_iters` MG-PCG iterations at full size after building its
-    CRS hierarchy (build time excluded)."""
+def oracle_lib(parallel):
+    """(library, threads, how): the oracle's OpenMP build on every host core
+    (one parallel loop per colour step and per SpMV, the parallelisation of the
+    reference code the paper compares with; the same bits as the plain build),
+    or the plain single-threaded build."""
+    import oracle.oracle as om
+    if parallel:
+        try:
+            lib = om.load_omp()
+            return lib, int(lib.orc_threads()), "OpenMP build (rows of each colour step and SpMV in parallel, dots sequential)"
+        except Exception as e:  # noqa: BLE001 - no OpenMP in the host compiler
+            return om._load(), 1, "single-threaded build (OpenMP build failed: %s)" % str(e)[:80]
+    return om._load(), 1, "single-threaded build"
+
+
+def cpu_baseline(steps_iters=None, nx=None, ny=None, nz=None, parallel=True):
+    """The CPU oracle, as it stands, on a bounded sample of the workload:
+    `steps_iters` MG-PCG iterations at full size after building its CRS
+    hierarchy (build time excluded)."""
     from oracle import OracleProblem
+    nx, ny, nz = nx or NX, ny or NY, nz or NZ
+    lib, threads, how = oracle_lib(parallel)
+    if steps_iters is None:  # about 5-10 s of CPU work either way
+        steps_iters = 24 if threads > 1 else 3
     t0 = time.perf_counter()
-    o = OracleProblem(nx, ny, nz, levels=LEVELS)
+    o = OracleProblem(nx, ny, nz, levels=LEVELS, lib=lib)
     b = o.rhs()
     t1 = time.perf_counter()
     o.pcg(b, max_iters=steps_iters, tol=0.0)
     t2 = time.perf_counter()
     fl = hpcg_flops_per_iter(nx, ny, nz, LEVELS) * steps_iters
-    return {"value": fl / (t2 - t1) / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": "%d MG-PCG iterations at %dx%dx%d (CRS build %.1f s excluded)" % (steps_iters, nx, ny, nz, t1 - t0),
-            "seconds": t2 - t1}
+    return {"value": fl / (t2 - t1) / 1e9, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": "%d MG-PCG iterations at %dx%dx%d, %s; CRS build %.1f s excluded" % (steps_iters, nx, ny, nz, how, t1 - t0),
+            "seconds": round(t2 - t1, 3)}
 
 
 def other_forms(dev, stream):
@@ -426,9 +479,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import OracleProblem
-    o = OracleProblem(NX, NY, NZ, levels=LEVELS)
+    lib, threads, how = oracle_lib(True)
+    o = OracleProblem(NX, NY, NZ, levels=LEVELS, lib=lib)
     b = o.rhs()
-    x = None
     for _ in range(args.warmup):
         o.pcg(b, max_iters=1, tol=0.0)
     t0 = time.perf_counter()
@@ -437,16 +490,15 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     fl = hpcg_flops_per_iter(NX, NY, NZ, LEVELS) * args.steps
     val = fl / dt / 1e9
-    line = {"impl": "reference", "metric": "HPCG-rule GFLOP/s at 192^3 (FP64 MG-PCG)", "value": val, "unit": "GFLOP/s",
+    sample = "1 MG-PCG iteration of the %dx%dx%d workload per step (the rate is per iteration, as the GPU arm's), %s" % (
+        NX, NY, NZ, how)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "FP64 MG-PCG 192^3, 4 levels, b=A*ones, x0=0; step = 1 CG iteration of the CPU oracle",
-                       "grid": [NX, NY, NZ], "levels": LEVELS},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "1 MG-PCG iteration at 192^3 per step",
-                             "value": val, "unit": "GFLOP/s"},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (HPCG generates its own operator; b = A*ones)", "config": bench_config(1),
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": val, "unit": "GFLOP/s"},
             "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-    del x
     return 0
 
 
@@ -507,6 +559,15 @@ def run_gpu(args):
     # correctness of the timed solve: exact solution is ones
     err_ones = float((x - 1.0).abs().max().item())
 
+    if args.profile_iters > 0:
+        # one solve of that many iterations inside cudaProfilerStart/Stop, for
+        # ncu --profile-from-start off (per-iteration kernel counters)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        x.zero_()
+        prob.pcg_solve(b, max_iters=args.profile_iters, tol=0.0, out=x)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": "HPCG-rule GFLOP/s (quick profiling run)", "value": value, "unit": "GFLOP/s",
@@ -527,18 +588,15 @@ def run_gpu(args):
     l0_ms = sorted(prob.profile_iteration(b)["smoother_ms"][0] for _ in range(5))[2]
     launches_l0 = 7 * 2
     k_ms = l0_ms / launches_l0
-    # Algorithmic bytes of the 14 launches (int64 mantissas of z, FP64 r):
-    # a full run reads z of every line (the off-line neighbours of a class are
-    # the other three classes, plus its own line: 8 n), r of its class lines
-    # (2 n) and writes its class lines (2 n): 12 n.  The pre-smoother starts
-    # from z = 0 and reads only the classes already written: [0,1] 4 n,
-    # [2,3] 6 n, [4,5] 8 n, [6,7,6] 10 n, then 3 x 12 n, + n for the restricted
-    # residual it writes; the post-smoother's first run also reads the coarse
-    # z (n), and its last run of each class writes z in FP64 (4 x 2 n).
-    # Total 158 n, 11.3 n per launch on average.  No FP64 instruction without
-    # kappa (the division by 26 is an integer multiply-high): HBM bounds it,
-    # 11.3 n / HBM = 11.8 us per launch at 192^3.
-    bytes_launch = 158 * n / launches_l0
+    # Algorithmic bytes (the method's, per row of the finest level and V-cycle):
+    # two symmetric smoother applications of 48 (r once, z read and written
+    # once per sweep direction), the residual with restriction 9, the
+    # refinement 2: 107 n over the 14 launches that carry them (restriction
+    # and refinement are fused into the smoother's runs).  The kernel itself
+    # moves more: every colour-pair run streams all of z to read its class's
+    # neighbours (12 n per full run, 158 n per V-cycle: traffic_model), which
+    # ncu's DRAM bytes confirm (traffic).
+    bytes_launch = 107 * n / launches_l0
     achieved_gbs = bytes_launch / (k_ms * 1e-3) / 1e9
     # DRAM traffic of one finest-level launch (post-smoother run [0,1]) from an
     # ncu capture at 192^3 (profiles/k_gs_lines_bfp_192cubed.md)
@@ -547,9 +605,11 @@ def run_gpu(args):
                 "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
                 "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
                 "bytes_algorithmic_per_launch": bytes_launch, "traffic": traffic,
-                "bytes_basis": "158 n per V-cycle over the 14 finest-level launches (12 n per full run)",
+                "traffic_model_per_launch": 158 * n / launches_l0,
+                "bytes_basis": "107 n per V-cycle (2 x 48 smoother + 9 restriction + 2 refinement) over the 14 finest-level "
+                               "launches; the kernel's own model 158 n (12 n per run: all of z per colour pair)",
                 "ms_per_launch": k_ms, "launches_timed": launches_l0,
-                "timing": "CUDA events around the finest level's two smoother applications (14 launches) of one CG iteration (hpcg_profile_iteration), median of 5",
+                "timing": "CUDA events around the finest level's 14 smoother launches of one CG iteration, median of 5",
                 "launch_shapes_per_level": shapes}
     # The FP64-storage colour kernel (k_gs_lines_fx: hpcg_rbgs, and the V-cycle
     # with block_fp = 0) for comparison: one symmetric sweep, 7 launches
@@ -642,20 +702,22 @@ def run_gpu(args):
     # kernel dominates (single-grid forms), and the whole solve against the
     # per-row byte model of algorithmic_bytes_per_iter
     mixed_l0_ms = breakdown["mixed"]["smoother_ms"][0]
-    mixed_l0_bytes = 74.5 * n  # FP32 analogue of the 158 n above: runs of 2, 3, 4, 5, 6, 6, 6 n (+ 0.5 n restricted
-    #                            residual) before the coarse correction, 7 x 6 n after it (refinement is its own kernel)
+    mixed_l0_bytes = 53.5 * n  # the method's 107 n with FP32 vectors (the kernels' own model: 74.5 n)
     # the binding roofline of one FP64 iteration, both terms: bytes over the
-    # copy bandwidth, and executed FP64 instructions (fixed-point sums leave 6
-    # FMA per finest-level row: p and x updates, r update and r.r, p.Ap, r.z)
-    # over the FP64 pipe (2 per SM per clock, 152 SMs)
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    # copy bandwidth, and the FP64-pipe warp instructions one iteration executes
+    # (ncu count per finest-level row) over the FP64 issue rate measured live
+    # by the library's probe
+    fp64_rate = fp64_probe(dev)
     bytes_us = algorithmic_bytes_per_iter(NX, NY, NZ, LEVELS) / (hbm_peak * 1e9) * 1e6
-    fp64_us = 6 * n / (2 * 152 * sm_mhz * 1e6) * 1e6
+    fp64_us = (FP64_WARP_INSTR_PER_ROW_ITER * n / fp64_rate["warp_instr_per_s"] * 1e6
+               if FP64_WARP_INSTR_PER_ROW_ITER is not None else 0.0)
     by_form = {
         "fp64_192^3_50_iters": {
             "dominant_kernel": roofline["kernel"], "dominant_kernel_frac": roofline["frac"],
             "whole_solve_roofline": whole_solve_roofline(algorithmic_bytes_per_iter(NX, NY, NZ, LEVELS) * ITERS, ms, hbm_peak),
             "binding_roofline_per_iter": {"bytes_term_us": bytes_us, "fp64_term_us": fp64_us,
+                                          "fp64_warp_instr_per_row": FP64_WARP_INSTR_PER_ROW_ITER,
+                                          "fp64_rate": fp64_rate,
                                           "bound": "hbm" if bytes_us >= fp64_us else "fp64",
                                           "measured_us": ms * 1e3 / ITERS,
                                           "frac": max(bytes_us, fp64_us) / (ms * 1e3 / ITERS)}},
@@ -707,37 +769,58 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank != 0:
         return 0
-    cpu = None
+    cpu = cpu1 = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(parallel=True)
+        cpu1 = cpu_baseline(parallel=False)
+    fp64_rate = by_form["fp64_192^3_50_iters"]["binding_roofline_per_iter"]["fp64_rate"]
+    if clocks.get("sm_mhz"):
+        fp64_rate["lane_fma_per_sm_clock"] = fp64_rate["lane_fma_per_s"] / fp64_rate["sms"] / (clocks["sm_mhz"] * 1e6)
+    detail = {
+        "roofline": roofline, "mixed_vs_fp64_to_1e-9": mixed_vs, "roofline_by_form": by_form, "spmv": spmv,
+        "iteration_breakdown": breakdown, "fp64_solve_variants": variants, "forms": forms, "hpcg_checks": checks,
+        "materialised_ell": ell, "cpu_baseline_1thread": cpu1, "ms_per_step_spread": [min(step_ms), max(step_ms)],
+    }
+    detail_path = args.detail or (os.path.join(ROOT, "gpurun_out", "bench_detail.json")
+                                  if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    if detail_path:
+        with open(detail_path, "w") as f:
+            json.dump(detail, f, indent=1, default=float)
+
+    def r3(v):
+        return None if v is None else float("%.4g" % v)
+
+    bw = by_form["fp64_192^3_50_iters"]
     line = {
-        "metric": "HPCG-rule GFLOP/s at 192^3 (FP64 MG-PCG); mixed vs FP64 time to 1e-9",
-        "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "ms_per_step_min": ms_min, "ms_per_step_spread": [min(step_ms), max(step_ms)],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (HPCG generates its own operator; b = A*ones)",
-        "config": {"workload": "FP64 MG-PCG 192^3, 4 levels (192/96/48/24), 1 pre + 1 post symmetric RBGS, "
-                               "50 CG iterations per step, b=A*ones, x0=0",
-                   "grid": [NX, NY, NZ], "levels": LEVELS, "cg_iters_per_step": ITERS,
-                   "l2": "working set (6 level-0 vectors = 340 MB) exceeds L2 (135.5 MB); no flush",
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "hpcg_gflop_per_iter": flops_iter / 1e9,
-        "ms_per_cg_iter": ms / ITERS,
-        "max_abs_err_vs_ones": err_ones,
+        "config": bench_config(world),
         "gpu_launches": launches,
-        "roofline": roofline,
-        "hbm_peak": {"value": peaks.get("hbm_gbs"), "kind": peak_kind},
-        "mixed_vs_fp64_to_1e-9": mixed_vs,
-        "roofline_by_form": by_form,
-        "spmv": spmv,
-        "iteration_breakdown": breakdown,
-        "fp64_solve_variants": variants,
-        "forms": forms,
-        "hpcg_checks": checks,
-        "materialised_ell": ell,
-        "e2e": e2e,
+        "roofline": {k: (r3(v) if isinstance(v, float) else v) for k, v in roofline.items()
+                     if k not in ("launch_shapes_per_level", "timing", "peak_basis", "fp64_storage_kernel")},
+        "hbm_gbs_whole_solve": r3(bw["whole_solve_roofline"]["gbs"]),
+        "mixed_vs_fp64_to_1e-9": {"fp64_ms": r3(mixed_vs["fp64"]["ms"]), "fp64_iters": mixed_vs["fp64"]["iters"],
+                                  "mixed_ms": r3(mixed_vs["mixed"]["ms"]), "mixed_iters": mixed_vs["mixed"]["iters"],
+                                  "mixed_restarts": mixed_vs["mixed"]["restarts"], "speedup": r3(mixed_vs["speedup"]),
+                                  "mixed_true_rel_res": r3(mixed_vs["mixed"]["true_rel_res"]),
+                                  "mixed_vs_fp64_x": r3(mixed_vs["mixed_vs_fp64_x"])},
+        "roofline_by_form": {k: {"kernel_frac": r3(v.get("dominant_kernel_frac")),
+                                 "whole_solve_frac": r3(v["whole_solve_roofline"]["frac"])}
+                             for k, v in by_form.items() if isinstance(v, dict) and "whole_solve_roofline" in v},
+        "binding_roofline_per_iter_us": {"bytes": r3(bw["binding_roofline_per_iter"]["bytes_term_us"]),
+                                         "fp64": r3(bw["binding_roofline_per_iter"]["fp64_term_us"]),
+                                         "measured": r3(bw["binding_roofline_per_iter"]["measured_us"]),
+                                         "fp64_tflops_probe": r3(fp64_rate["tflops"])},
+        "spmv_hbm_frac": r3(spmv["hbm_frac_of_measured"]),
+        "smoother_ms_per_level": [r3(v) for v in breakdown["fp64"]["smoother_ms"]],
+        "iter_ms": r3(breakdown["fp64"]["total_ms"]),
+        "max_abs_err_vs_ones": r3(err_ones),
+        "e2e": {k: (r3(v) if isinstance(v, float) else v) for k, v in e2e.items()},
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "cpu_baseline_1thread_gflops": r3(cpu1["value"]) if cpu1 else None,
+        "detail": os.path.relpath(detail_path, ROOT) if detail_path else None,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -761,6 +844,11 @@ def main():
     ap.add_argument("--ell-only", action="store_true",
                     help="run only the materialised-operator study (sliced-ELL, colour-sorted and natural order, two "
                          "sub-domains) at the grid size and print its JSON (profiling runs)")
+    ap.add_argument("--detail", default=None,
+                    help="file for the full measurement record (default gpurun_out/bench_detail.json when that folder exists)")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="after the timed steps, one solve of this many CG iterations between cudaProfilerStart and "
+                         "cudaProfilerStop (for ncu --profile-from-start off)")
     ap.add_argument("--quick", action="store_true",
                     help="time the FP64 solve only (no kernel roofline, mixed comparison, e2e or CPU baseline)")
     args = ap.parse_args()

@@ -452,6 +452,20 @@ int hpcg_split_mg_vcycle(hpcg_split_handle h, const double *r_dev, double *z_dev
 int hpcg_split_pcg_solve(hpcg_split_handle h, const double *b_dev, double *x_dev, int max_iters, double rel_tol,
                          hpcg_stats *stats, void *stream);
 
+/* --- measurement aid ------------------------------------------------------------------ */
+/* Not part of the paper: the FP64 fused multiply-add issue rate of the current
+ * GPU, the denominator of the FP64 term of a binding roofline (on this GPU the
+ * FP64 pipe is narrow enough to bind some kernels before memory does).  Launches
+ * `blocks` blocks of 256 threads, each thread 8 independent chains of `iters`
+ * dependent FMAs (one untimed warm-up launch, then one launch timed with CUDA
+ * events on `stream`); sink_dev (device, blocks*256 doubles, caller-owned)
+ * receives each thread's sum so that no FMA is optimised away.  *ms_host gets
+ * the timed launch's milliseconds and *fma_host the FMA instructions it
+ * executed per thread summed over threads (divide by 32 for warp-level
+ * instructions).  Synchronises `stream`.  Errors: INVALID_ARG for a
+ * non-positive count or null pointer; CUDA for a failed launch. */
+int hpcg_probe_fp64_rate(int blocks, int iters, double *sink_dev, double *ms_host, double *fma_host, void *stream);
+
 /* --- diagnostics ------------------------------------------------------------------ */
 const char *hpcg_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (thread-unsafe). */

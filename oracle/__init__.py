@@ -18,4 +18,5 @@ against closed forms, brute force, dense textbook routines or dense direct
 solves; the exact per-iteration residual history is pinned only through
 those properties (the paper prints no worked example).
 """
-from .oracle import (OracleProblem, build_oracle, spmv_rows, lib_path, solve_and_grad)  # noqa: F401
+from .oracle import (OracleProblem, build_oracle, build_oracle_omp, load_omp, spmv_rows, lib_path,  # noqa: F401
+                     solve_and_grad)

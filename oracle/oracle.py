@@ -39,6 +39,26 @@ def build_oracle(force=False):
     return compile_source(_SRC, out)
 
 
+def omp_lib_path():
+    return os.path.join(_OUT_DIR, "libhpcg_oracle_omp.so")
+
+
+def build_oracle_omp(force=False):
+    """The same source built with -fopenmp: each SpMV's and each colour step's
+    rows in one parallel loop (same bits as the plain build); the CPU
+    baseline on all host cores.  Raises if the compiler has no OpenMP."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    out = omp_lib_path()
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    return compile_source(_SRC, out, extra=("-fopenmp",))
+
+
+def load_omp():
+    """The OpenMP build, loaded (its thread count follows OMP_NUM_THREADS)."""
+    return load_library(build_oracle_omp())
+
+
 _d = ctypes.POINTER(ctypes.c_double)
 _i = ctypes.POINTER(ctypes.c_int)
 _l = ctypes.POINTER(ctypes.c_long)
@@ -65,6 +85,8 @@ def _declare(lib):
     lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d]
     lib.orc_free.argtypes = [_vp]
     lib.orc_set_symmetric.argtypes = [_vp, ctypes.c_int]
+    lib.orc_threads.restype = ctypes.c_int
+    lib.orc_threads.argtypes = []
     lib.orc_levels.argtypes = [_vp]
     lib.orc_level_n.restype = ctypes.c_long
     lib.orc_level_n.argtypes = [_vp, ctypes.c_int]

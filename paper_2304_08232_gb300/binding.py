@@ -517,17 +517,24 @@ class HpcgSolve(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, b, kappa, problem, max_iters, tol):
-        problem.set_kappa(kappa.detach().contiguous())
+        kd = kappa.detach().contiguous()
+        problem.set_kappa(kd)
         x, st = problem.pcg_solve(b.detach().contiguous(), max_iters=max_iters, tol=tol)
         ctx.problem, ctx.max_iters, ctx.tol = problem, max_iters, tol
-        ctx.save_for_backward(x)
+        # kappa is saved too (autograd then refuses a backward after an in-place
+        # change of it): the adjoint solve must use this forward's operator even
+        # if the problem solved with another kappa in between
+        ctx.save_for_backward(x, kappa)
+        ctx.kappa_used = kd
         ctx.forward_stats = st
         problem.last_forward_stats = st
         return x
 
     @staticmethod
     def backward(ctx, grad_x):
-        (x,) = ctx.saved_tensors
+        x, _ = ctx.saved_tensors
+        if getattr(ctx.problem, "_kappa_ref", None) is not ctx.kappa_used:
+            ctx.problem.set_kappa(ctx.kappa_used)
         gb, gk, st = ctx.problem.pcg_backward(x, grad_x.contiguous(), max_iters=ctx.max_iters, tol=ctx.tol,
                                               want_kappa=ctx.needs_input_grad[1])
         ctx.problem.last_backward_stats = st

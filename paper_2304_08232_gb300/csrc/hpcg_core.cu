@@ -1241,6 +1241,25 @@ static int enqueue_x_pending(hpcg_ctx *h, double *x, cudaStream_t s) {
   return HPCG_OK;
 }
 
+// flag[0] = 1 once every instance of a batch has finished its solve (the
+// batch's convergence flag, polled by the host like a single grid's done).
+__global__ void k_all_done(const CgState *__restrict__ st, int count, int *flag) {
+  pdl_enter();
+  int ok = 1;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) ok &= st[i].done != 0;
+  ok = __syncthreads_and(ok);
+  if (threadIdx.x == 0) *flag = ok;
+}
+
+// The pinned flag slots and events of the convergence poll, made on the
+// first tolerance solve of the handle (cudaMallocHost synchronises the device).
+static int ensure_poll(hpcg_ctx *h) {
+  if (!h->poll_flags) CK(cudaMallocHost(&h->poll_flags, sizeof(int) * 2));
+  for (int k = 0; k < 2; ++k)
+    if (!h->poll_ev[k]) CK(cudaEventCreateWithFlags(&h->poll_ev[k], cudaEventDisableTiming));
+  return HPCG_OK;
+}
+
 static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, double tol, hpcg_stats *stats, cudaStream_t s) {
   if (max_iters < 0 || max_iters > kHistoryCap) return HPCG_ERR_INVALID_ARG;
   TRY(reset_error_word(h, s));
@@ -1250,13 +1269,8 @@ static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, doubl
   TRY(get_iter_graph(h, b, x, &exec, &nk));
   const int every = h->opt.check_every > 0 ? h->opt.check_every : 1;
   std::vector<CgState> hs(h->count);
-  int *pinned = nullptr;
-  if (tol > 0.0) CK(cudaMallocHost(&pinned, sizeof(int) * 2));
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  if (tol > 0.0) {
-    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-  }
+  if (tol > 0.0) TRY(ensure_poll(h));
+  int *const all_done = (int *)(h->ws + h->o_sync + 16);  // batches: every instance done
   int rc = HPCG_OK;
   int pending = -1;  // slot whose flag copy is in flight
   for (int it = 0; it < max_iters; ++it) {
@@ -1267,29 +1281,26 @@ static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, doubl
     }
     g_launches.fetch_add(nk);
     if (tol > 0.0 && ((it + 1) % every == 0)) {
-      // all instances done <=> min over done flags; single instance: st[0].done.
-      // For batches the host polls instance 0..count-1 through the stats copy below;
-      // here only the first instance's flag is sampled when count == 1.
-      if (h->count == 1) {
-        const int slot = it & 1;
-        e = cudaMemcpyAsync(pinned + slot, &h->st[0].done, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[slot], s);
-        if (e != cudaSuccess) {
-          rc = cuda_fail(e, "flag copy");
-          break;
-        }
-        if (pending >= 0) {
-          cudaEventSynchronize(ev[pending]);
-          if (pinned[pending]) break;
-        }
-        pending = slot;
-      } else {
-        CK(cudaMemcpyAsync(hs.data(), h->st, sizeof(CgState) * h->count, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        bool all = true;
-        for (auto &c : hs) all = all && c.done;
-        if (all) break;
+      // the host reads the flag of the iteration before this one while the GPU
+      // runs this one (one iteration of lag; iterations enqueued after
+      // convergence are no-ops on the device): a single grid's done, or the
+      // all-done flag of a batch
+      const int slot = it & 1;
+      const int *flag = &h->st[0].done;
+      if (h->count > 1) {
+        e = launch_k(k_all_done, dim3(1), dim3(256), 0, s, (const CgState *)h->st, h->count, all_done);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        flag = all_done;
       }
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->poll_flags + slot, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaEventRecord(h->poll_ev[slot], s);
+      if (e == cudaSuccess && pending >= 0) e = cudaEventSynchronize(h->poll_ev[pending]);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "convergence flag poll");
+        break;
+      }
+      if (pending >= 0 && h->poll_flags[pending]) break;
+      pending = slot;
     }
   }
   if (rc == HPCG_OK) rc = enqueue_x_pending(h, x, s);
@@ -1298,9 +1309,6 @@ static int run_pcg(hpcg_ctx *h, const double *b, double *x, int max_iters, doubl
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = cuda_fail(e, "stats copy");
   }
-  if (ev[0]) cudaEventDestroy(ev[0]);
-  if (ev[1]) cudaEventDestroy(ev[1]);
-  if (pinned) cudaFreeHost(pinned);
   if (rc != HPCG_OK) return rc;
   int worst = HPCG_OK;
   for (int i = 0; i < h->count; ++i) {
@@ -1651,6 +1659,9 @@ int hpcg_destroy(hpcg_handle h) {
   if (!h) return HPCG_ERR_INVALID_ARG;
   if (h->ready) cudaDeviceSynchronize();
   if (h->g_iter.exec) cudaGraphExecDestroy(h->g_iter.exec);
+  for (cudaEvent_t e : h->poll_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->poll_flags) cudaFreeHost(h->poll_flags);
   if (h->multi) hpcg_destroy(h->multi);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ws_owned && h->ws) cudaFree(h->ws);

@@ -91,12 +91,16 @@ struct hpcg_ctx {
   bool tail_ok = true;        // cleared if a cooperative launch is refused
   int tail_grid = 0;
   long long wait_limit = 2000000000LL;  // clock cycles a grid barrier may wait (about 1 s)
-  size_t o_tail = 0, o_sync = 0;        // TailPlan[2] (FP64, FP32) and {barrier count, generation, error}
+  size_t o_tail = 0, o_sync = 0;        // TailPlan[2] (FP64, FP32); {barrier count, generation, error, -, batch all-done flag}
   // cluster kernel of the block-floating-point V-cycle's coarse end (levels bfp_tail_first..levels-1)
   int bfp_tail_first = -1;  // -1: none
   int bfp_tail_ok = -1;     // -1: not checked yet; 0: the GPU cannot run the cluster
   size_t o_tail_bfp = 0;    // BfpTailPlan
   int fin_cluster_ok = -1;  // -1: not checked yet; 1: per-line reductions finalise in a cluster (k_finalize_lines)
+  // tolerance solves: two pinned flag slots and their events for the host's
+  // one-iteration-lag poll of the convergence flag (made once per handle)
+  int *poll_flags = nullptr;
+  cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   int device = 0;
   std::mutex mu;
 };

@@ -51,3 +51,23 @@ def test_whole_solve_roofline_and_job_value():
     r = bench.whole_solve_roofline(6.0e9, 1.0, 6000.0)
     assert r["gbs"] == pytest.approx(6000.0) and r["frac"] == pytest.approx(1.0)
     assert bench.whole_job_gflops(4, 2.0e9, 10.0) == pytest.approx(800.0)
+
+
+def test_both_arms_report_the_same_metric_and_config(capsys, monkeypatch):
+    """The reference arm (the CPU oracle) prints the GPU arm's metric, unit,
+    direction and config, so that their values can be divided; here on a
+    small grid so that it runs in a second."""
+    import json
+
+    class A:
+        steps, warmup, gpus = 1, 0, 1
+    monkeypatch.setattr(bench, "NX", 16)
+    monkeypatch.setattr(bench, "NY", 16)
+    monkeypatch.setattr(bench, "NZ", 16)
+    assert bench.run_reference(A()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == "GFLOP/s" and line["higher_is_better"] is True
+    assert line["config"] == bench.bench_config(1)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["value"] == line["value"]

@@ -120,6 +120,30 @@ def test_differentiable_solve_gradients():
         assert normwise(host(kt.grad), gkr) <= 1e-10
 
 
+def test_two_solves_on_one_problem_keep_their_own_operators():
+    """Two forward solves with different kappa on one problem, one backward
+    through both: each adjoint solve must use its own forward's operator."""
+    from paper_2304_08232_gb300 import HpcgProblem, hpcg_solve
+    need_gpu()
+    dims, levels = (8, 8, 8), 3
+    n = 512
+    k1, b, xt = differentiable_inputs(n, seed=4)
+    k2 = k1[::-1].copy() * 3.0
+    g = HpcgProblem(*dims, levels=levels)
+    bt = dev(b).requires_grad_(True)
+    kt1 = dev(k1).requires_grad_(True)
+    kt2 = dev(k2).requires_grad_(True)
+    x1 = hpcg_solve(bt, kt1, g, max_iters=300, tol=1e-13)
+    x2 = hpcg_solve(bt, kt2, g, max_iters=300, tol=1e-13)
+    loss = 0.5 * ((x1 - dev(xt)) ** 2).sum() + 0.5 * ((x2 - dev(xt)) ** 2).sum()
+    loss.backward()
+    _, _, gb1, gk1 = solve_and_grad(dims, levels, k1, b, xt)
+    _, _, gb2, gk2 = solve_and_grad(dims, levels, k2, b, xt)
+    assert normwise(host(kt1.grad), gk1) <= 1e-10
+    assert normwise(host(kt2.grad), gk2) <= 1e-10
+    assert normwise(host(bt.grad), gb1 + gb2) <= 1e-10
+
+
 def test_kappa_solve_matches_oracle():
     from paper_2304_08232_gb300 import HpcgProblem
     need_gpu()
