@@ -466,6 +466,15 @@ int hpcg_split_pcg_solve(hpcg_split_handle h, const double *b_dev, double *x_dev
  * non-positive count or null pointer; CUDA for a failed launch. */
 int hpcg_probe_fp64_rate(int blocks, int iters, double *sink_dev, double *ms_host, double *fma_host, void *stream);
 
+/* Diagnostic, not part of the paper: the int64 -> FP64 conversion that the
+ * fixed-point and block-floating-point kernels build on the integer pipe,
+ * out_dev[i] = q_i 2^(E_i - 1080) rounded to nearest (ties to even), beside
+ * ref_dev[i] = CUDA's round-to-nearest __ll2double_rn(q_i) scaled exactly by
+ * 2^(E_i - 1080), for n pairs (device arrays: q int64 with |q_i| < 2^63, E int32
+ * in [64, 2000], outputs FP64).  The two agree bit for bit when the kernels'
+ * conversion is right.  Errors: INVALID_ARG for n < 0 or a null pointer. */
+int hpcg_fx_to_double_check(long n, const long long *q_dev, const int *e_dev, double *out_dev, double *ref_dev, void *stream);
+
 /* --- diagnostics ------------------------------------------------------------------ */
 const char *hpcg_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (thread-unsafe). */

@@ -85,6 +85,7 @@ SIGNATURES = {
     "hpcg_split_mg_vcycle": (_i, [_vp, _vp, _vp, _vp]),
     "hpcg_split_pcg_solve": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
     "hpcg_probe_fp64_rate": (_i, [_i, _i, _vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
+    "hpcg_fx_to_double_check": (_i, [_l, _vp, _vp, _vp, _vp, _vp]),
     "hpcg_strerror": (ctypes.c_char_p, [_i]),
     "hpcg_last_cuda_error": (ctypes.c_char_p, []),
     "hpcg_launch_count": (_l, []),

@@ -18,6 +18,7 @@
 #include "hpcg_tail.cuh"
 #include "hpcg_fixed.cuh"
 #include "hpcg_bfp.cuh"
+#include "hpcg_spmv.cuh"
 
 using namespace hpcg;
 
@@ -691,6 +692,21 @@ template <typename T, int N, int Mode>
 static void launch_spmv_lines(hpcg_ctx *h, const LevelData &L, const T *x, const T *b, T *y, const T *kap, double *partials,
                               const CgState *st, cudaStream_t s) {
   const dim3 blk(32, L.tab.row_lpc);
+  if constexpr (sizeof(T) == 8 && N <= 6) {  // lines of up to 192 points: each plane staged once per block
+    if (h->opt.fixed_point && L.tab.row_lpc <= kSpmvMaxLpc) {
+      // opt in to more than 48 KB of dynamic shared memory, once per device and instantiation
+      static std::atomic<unsigned long long> smem_set{0};
+      const unsigned long long bit = 1ULL << (h->device & 63);
+      if (!(smem_set.load(std::memory_order_relaxed) & bit)) {
+        cudaFuncSetAttribute(k_spmv_stage_fx<N, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_stage_smem<N>(kSpmvMaxLpc));
+        smem_set.fetch_or(bit);
+      }
+      const int vec16 = L.even_nx && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+      launch_k(k_spmv_stage_fx<N, Mode>, L.tab.nblk_row, blk, spmv_stage_smem<N>(L.tab.row_lpc), s, L.tab.inst, h->count, L.tab.row_lpc,
+               L.tab.row_zc, x, b, y, kap, partials, st, vec16);
+      return;
+    }
+  }
   if constexpr (sizeof(T) == 8 && N <= 8) {
     if (h->opt.fixed_point) {
       launch_k(k_spmv_lines_fx<N, Mode>, L.tab.nblk_row, blk, 0, s, L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y, kap, partials,

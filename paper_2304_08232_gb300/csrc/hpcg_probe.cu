@@ -59,3 +59,27 @@ extern "C" int hpcg_probe_fp64_rate(int blocks, int iters, double *sink_dev, dou
   cudaEventDestroy(e1);
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Diagnostic: the integer-pipe int64 -> FP64 conversion of the fixed-point and
+// block-floating-point kernels, beside CUDA's own conversion.
+#include "hpcg_fixed.cuh"
+
+namespace {
+__global__ void k_fx_to_double_check(long n, const long long *__restrict__ q, const int *__restrict__ e, double *__restrict__ out,
+                                     double *__restrict__ ref) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = hpcg::fx_to_double(q[i], e[i]);
+  ref[i] = ldexp(__ll2double_rn(q[i]), e[i] - 1080);  // rounded once, then scaled exactly by a power of two
+}
+}  // namespace
+
+extern "C" int hpcg_fx_to_double_check(long n, const long long *q_dev, const int *e_dev, double *out_dev, double *ref_dev,
+                                       void *stream) {
+  if (n < 0 || (n > 0 && (!q_dev || !e_dev || !out_dev || !ref_dev))) return HPCG_ERR_INVALID_ARG;
+  if (n == 0) return HPCG_OK;
+  k_fx_to_double_check<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, q_dev, e_dev, out_dev, ref_dev);
+  CKL("k_fx_to_double_check");
+  return HPCG_OK;
+}
