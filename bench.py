@@ -849,6 +849,10 @@ def main():
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="after the timed steps, one solve of this many CG iterations between cudaProfilerStart and "
                          "cudaProfilerStop (for ncu --profile-from-start off)")
+    ap.add_argument("--vcycles", type=int, default=0,
+                    help="time this many V-cycles alone and print per-level times (profiling runs of the preconditioner)")
+    ap.add_argument("--cluster-tail", action="store_true", help="with --vcycles: hpcg_options.cluster_tail")
+    ap.add_argument("--persistent", action="store_true", help="with --vcycles: hpcg_options.persistent")
     ap.add_argument("--quick", action="store_true",
                     help="time the FP64 solve only (no kernel roofline, mixed comparison, e2e or CPU baseline)")
     args = ap.parse_args()
@@ -860,7 +864,39 @@ def main():
         return run_reference(args)
     if args.ell_only:
         return run_ell_only()
+    if args.vcycles > 0:
+        return run_vcycles(args)
     return run_gpu(args)
+
+
+def run_vcycles(args):
+    """Profiling runs of the preconditioner alone: `--vcycles K` V-cycles
+    (z = M r, r ~ N(0,1)) on the grid, with the coarse-end options given,
+    timed with CUDA events; prints one JSON line with the per-level times of
+    one CG iteration (hpcg_profile_iteration) as well."""
+    import torch
+    from hpcg_inputs import normal
+    from paper_2304_08232_gb300 import HpcgProblem
+    dev = torch.device("cuda", 0)
+    prob = HpcgProblem(NX, NY, NZ, levels=LEVELS, precision=args.precision, cluster_tail=args.cluster_tail,
+                       persistent=args.persistent, device=dev)
+    r = torch.as_tensor(normal(NX * NY * NZ, 0), device=dev)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        prob.mg_vcycle(r, out=z)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.vcycles):
+        prob.mg_vcycle(r, out=z)
+    e1.record()
+    torch.cuda.synchronize()
+    pr = prob.profile_iteration(prob.get_rhs())
+    print(json.dumps({"grid": [NX, NY, NZ], "cluster_tail": args.cluster_tail, "persistent": args.persistent,
+                      "precision": args.precision, "ms_per_vcycle": e0.elapsed_time(e1) / args.vcycles,
+                      "iteration_profile": pr}), flush=True)
+    return 0
 
 
 def run_ell_only():

@@ -386,6 +386,37 @@ __global__ void __launch_bounds__(256) k_gs_lines_bfp(const Inst *__restrict__ t
                           zout, dpart, zqc, zec, tabcp);
 }
 
+// The same runs for a batch whose instances have x-lines of different lengths:
+// each block belongs to one instance and takes the narrowest register window
+// that holds that instance's lines (a launch sized for the widest line would
+// leave most lanes of a short line idle).  Same arithmetic per line, so the
+// same bits as k_gs_lines_bfp.
+template <int NC>
+__global__ void __launch_bounds__(256) k_gs_lines_bfp_batch(const Inst *__restrict__ tab, int count, int lpc, int zc, int py, int pz, int pa,
+                                                            int steps, int vmask, const double *__restrict__ r, long long *__restrict__ zq,
+                                                            int *__restrict__ ze, const double *__restrict__ invd,
+                                                            const CgState *__restrict__ st, const Inst *__restrict__ tabc,
+                                                            double *__restrict__ rc, const double *__restrict__ kap, double *__restrict__ zout,
+                                                            double *__restrict__ dpart, const long long *__restrict__ zqc,
+                                                            const int *__restrict__ zec, const Inst *__restrict__ tabcp, const Inst g1) {
+  pdl_enter();
+  const int nxi = tab[find_inst<4>(tab, count, blockIdx.x)].nx;
+  if (nxi <= 64) {
+    gs_bfp_block<1, false>(blockIdx.x, threadIdx.y, tab, g1, count, lpc, zc, py, pz, pa, steps, vmask, r, zq, ze, invd, st, tabc, rc, kap,
+                           zout, dpart, zqc, zec, tabcp);
+    return;
+  }
+  if constexpr (NC > 2) {
+    if (nxi <= 128) {
+      gs_bfp_block<2, false>(blockIdx.x, threadIdx.y, tab, g1, count, lpc, zc, py, pz, pa, steps, vmask, r, zq, ze, invd, st, tabc, rc,
+                             kap, zout, dpart, zqc, zec, tabcp);
+      return;
+    }
+  }
+  gs_bfp_block<NC, false>(blockIdx.x, threadIdx.y, tab, g1, count, lpc, zc, py, pz, pa, steps, vmask, r, zq, ze, invd, st, tabc, rc, kap,
+                          zout, dpart, zqc, zec, tabcp);
+}
+
 // The refinement fused into a post-smoother's first run, alone: the same
 // block work as k_gs_lines_bfp (same launch shape and arguments), stopping
 // once the refined class (0,0) line is stored (hpcg_mg_stage).

@@ -694,16 +694,19 @@ static void launch_spmv_lines(hpcg_ctx *h, const LevelData &L, const T *x, const
   const dim3 blk(32, L.tab.row_lpc);
   if constexpr (sizeof(T) == 8 && N <= 6) {  // lines of up to 192 points: each plane staged once per block
     if (h->opt.fixed_point && L.tab.row_lpc <= kSpmvMaxLpc) {
-      // opt in to more than 48 KB of dynamic shared memory, once per device and instantiation
-      static std::atomic<unsigned long long> smem_set{0};
+      // a batch: each block takes the register window of its instance's lines
+      auto kern = (h->count > 1 && N > 1) ? k_spmv_stage_fx_batch<N, Mode> : k_spmv_stage_fx<N, Mode>;
+      // opt in to more than 48 KB of dynamic shared memory, once per device and kernel
+      static std::atomic<unsigned long long> smem_set[2] = {{0}, {0}};
+      const int which = kern == k_spmv_stage_fx<N, Mode> ? 0 : 1;
       const unsigned long long bit = 1ULL << (h->device & 63);
-      if (!(smem_set.load(std::memory_order_relaxed) & bit)) {
-        cudaFuncSetAttribute(k_spmv_stage_fx<N, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_stage_smem<N>(kSpmvMaxLpc));
-        smem_set.fetch_or(bit);
+      if (!(smem_set[which].load(std::memory_order_relaxed) & bit)) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_stage_smem<N>(kSpmvMaxLpc));
+        smem_set[which].fetch_or(bit);
       }
       const int vec16 = L.even_nx && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
-      launch_k(k_spmv_stage_fx<N, Mode>, L.tab.nblk_row, blk, spmv_stage_smem<N>(L.tab.row_lpc), s, L.tab.inst, h->count, L.tab.row_lpc,
-               L.tab.row_zc, x, b, y, kap, partials, st, vec16);
+      launch_k(kern, L.tab.nblk_row, blk, spmv_stage_smem<N>(L.tab.row_lpc), s, L.tab.inst, h->count, L.tab.row_lpc, L.tab.row_zc, x, b, y,
+               kap, partials, st, vec16);
       return;
     }
   }
@@ -770,6 +773,14 @@ static void launch_gs_bfp(const LevelData &L, int count, int py, int pz, int pa,
     // steps == 0 there is the refinement alone)
     if (split && L.tab.line_lpc <= kBfpSplitMaxLines) {
       launch_k(k_gs_lines_bfp_split<NC>, dim3(L.tab.nblk_line), dim3(32, NC * L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc,
+               L.tab.line_zc, py, pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart,
+               C ? (const long long *)C->zq : nullptr, C ? (const int *)C->ze : nullptr, C ? C->tab.inst : nullptr, L.inst[0]);
+      return;
+    }
+  }
+  if constexpr (NC == 2 || NC == 3) {
+    if (count > 1 && !refine_only) {  // a batch: each block takes the register window of its instance's lines
+      launch_k(k_gs_lines_bfp_batch<NC>, dim3(L.tab.nblk_line), dim3(32, L.tab.line_lpc), 0, s, L.tab.inst, count, L.tab.line_lpc,
                L.tab.line_zc, py, pz, pa, steps, vmask, r, L.zq, L.ze, invd, st, tabc, rc, kap, zout, dpart,
                C ? (const long long *)C->zq : nullptr, C ? (const int *)C->ze : nullptr, C ? C->tab.inst : nullptr, L.inst[0]);
       return;

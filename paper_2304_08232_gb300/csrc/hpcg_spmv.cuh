@@ -130,20 +130,17 @@ __host__ __device__ constexpr size_t spmv_stage_smem(int lpc) {
   return (size_t)4 * (lpc + 2) * 32 * NC * sizeof(long long) + (size_t)4 * (lpc + 2) * sizeof(int);
 }
 
+// The work of one block (instance ii).
 template <int NC, int Mode>
-__global__ void __launch_bounds__(32 * kSpmvMaxLpc) k_spmv_stage_fx(const Inst *__restrict__ tab, int count, int lpc, int zc,
-                                                                     const double *__restrict__ x, const double *__restrict__ b,
-                                                                     double *__restrict__ y, const double *__restrict__ kap,
-                                                                     double *__restrict__ partials, const CgState *__restrict__ st,
-                                                                     int vec16) {
-  pdl_enter();
-  extern __shared__ __align__(16) long long smem_spmv[];
+__device__ __forceinline__ void spmv_stage_block(const Inst *__restrict__ tab, int count, int ii, int lpc, int zc, const double *__restrict__ x,
+                                                 const double *__restrict__ b, double *__restrict__ y, const double *__restrict__ kap,
+                                                 double *__restrict__ partials, const CgState *__restrict__ st, int vec16,
+                                                 long long *__restrict__ smem_spmv) {
   const int nslot = lpc + 2;
   const int bstride = nslot * 32 * NC;  // one plane buffer
   long long *const sq = smem_spmv;
   int *const se = reinterpret_cast<int *>(smem_spmv + 4 * bstride);  // [4][nslot]
   const int blk = blockIdx.x;
-  const int ii = count == 1 ? 0 : find_inst<3>(tab, count, blk);
   const Inst g = tab[ii];
   const int w = threadIdx.y, lane = threadIdx.x;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -281,6 +278,42 @@ __global__ void __launch_bounds__(32 * kSpmvMaxLpc) k_spmv_stage_fx(const Inst *
     bc = bn;
   }
   cp_async_wait<0>();  // the last fetch (beyond the block's planes) lands before the block ends
+}
+
+template <int NC, int Mode>
+__global__ void __launch_bounds__(32 * kSpmvMaxLpc) k_spmv_stage_fx(const Inst *__restrict__ tab, int count, int lpc, int zc,
+                                                                     const double *__restrict__ x, const double *__restrict__ b,
+                                                                     double *__restrict__ y, const double *__restrict__ kap,
+                                                                     double *__restrict__ partials, const CgState *__restrict__ st,
+                                                                     int vec16) {
+  pdl_enter();
+  extern __shared__ __align__(16) long long smem_spmv[];
+  const int ii = count == 1 ? 0 : find_inst<3>(tab, count, blockIdx.x);
+  spmv_stage_block<NC, Mode>(tab, count, ii, lpc, zc, x, b, y, kap, partials, st, vec16, smem_spmv);
+}
+
+// The same for a batch whose instances have x-lines of different lengths:
+// each block (one instance) takes the narrowest register window that holds
+// its lines (the launch's shared memory, sized for the widest, holds it).
+// Same arithmetic per line, so the same bits as k_spmv_stage_fx.
+template <int NC, int Mode>
+__global__ void __launch_bounds__(32 * kSpmvMaxLpc) k_spmv_stage_fx_batch(const Inst *__restrict__ tab, int count, int lpc, int zc,
+                                                                           const double *__restrict__ x, const double *__restrict__ b,
+                                                                           double *__restrict__ y, const double *__restrict__ kap,
+                                                                           double *__restrict__ partials, const CgState *__restrict__ st,
+                                                                           int vec16) {
+  pdl_enter();
+  extern __shared__ __align__(16) long long smem_spmv[];
+  const int ii = find_inst<3>(tab, count, blockIdx.x);
+  const int nxi = tab[ii].nx;
+  if (nxi <= 32) return spmv_stage_block<1, Mode>(tab, count, ii, lpc, zc, x, b, y, kap, partials, st, vec16, smem_spmv);
+  if constexpr (NC > 2) {
+    if (nxi <= 64) return spmv_stage_block<2, Mode>(tab, count, ii, lpc, zc, x, b, y, kap, partials, st, vec16, smem_spmv);
+  }
+  if constexpr (NC > 3) {
+    if (nxi <= 96) return spmv_stage_block<3, Mode>(tab, count, ii, lpc, zc, x, b, y, kap, partials, st, vec16, smem_spmv);
+  }
+  spmv_stage_block<NC, Mode>(tab, count, ii, lpc, zc, x, b, y, kap, partials, st, vec16, smem_spmv);
 }
 
 }  // namespace hpcg
