@@ -476,6 +476,17 @@ int hpcg_probe_fp64_rate(int blocks, int iters, double *sink_dev, double *ms_hos
 int hpcg_fx_to_double_check(long n, const long long *q_dev, const int *e_dev, double *out_dev, double *ref_dev, void *stream);
 
 /* --- diagnostics ------------------------------------------------------------------ */
+/* Bounds-checking build (not part of the paper; the library compiled with
+ * -DHPCG_BOUNDS_CHECK, paper_2304_08232_gb300/build.py build_checked): the
+ * kernels of the default FP64 path (colour-pair runs in block floating point,
+ * the staged SpMV, the CG updates, dot products and reductions, the level-vector
+ * conversions) check every index range they touch against its array's extent;
+ * a miss is counted, the first one recorded, and the access skipped (nothing
+ * traps).  Synchronises with the device (a symbol copy).  *count_host receives
+ * the violations since the last reset, first_host[0..1] the source line of the
+ * first one and its index (-1, -1 if none); reset != 0 clears the record.
+ * Returns UNSUPPORTED from the normal build (count 0). */
+int hpcg_bounds_status(long long *count_host, long long *first_host, int reset);
 const char *hpcg_strerror(int status);
 /* Text of the last CUDA error seen by the library in this process (thread-unsafe). */
 const char *hpcg_last_cuda_error(void);

@@ -86,6 +86,7 @@ SIGNATURES = {
     "hpcg_split_pcg_solve": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
     "hpcg_probe_fp64_rate": (_i, [_i, _i, _vp, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
     "hpcg_fx_to_double_check": (_i, [_l, _vp, _vp, _vp, _vp, _vp]),
+    "hpcg_bounds_status": (_i, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _i]),
     "hpcg_strerror": (ctypes.c_char_p, [_i]),
     "hpcg_last_cuda_error": (ctypes.c_char_p, []),
     "hpcg_launch_count": (_l, []),
@@ -99,6 +100,15 @@ STAGE_PRE, STAGE_REFINE, STAGE_POST = 0, 1, 2
 _LIB = None
 
 
+def _open(path):
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
 def load(path=None):
     """Loads the built library (no build here); raises ImportError if absent."""
     global _LIB
@@ -108,13 +118,20 @@ def load(path=None):
     if not os.path.exists(path):
         raise ImportError("CUDA library %s is missing: build it with "
                           "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
-    lib = ctypes.CDLL(path)
-    for name, (res, args) in SIGNATURES.items():
-        fn = getattr(lib, name)
-        fn.restype = res
-        fn.argtypes = args
-    _LIB = lib
-    return lib
+    _LIB = _open(path)
+    return _LIB
+
+
+_LIB_CHECKED = None
+
+
+def load_checked():
+    """The bounds-checking build of the library (built on first use with
+    build.build_checked; a second library beside the normal one)."""
+    global _LIB_CHECKED
+    if _LIB_CHECKED is None:
+        _LIB_CHECKED = _open(_build.build_checked())
+    return _LIB_CHECKED
 
 
 class HpcgError(RuntimeError):

@@ -59,8 +59,8 @@ class HpcgProblem:
 
     def __init__(self, nx, ny, nz, levels=4, precision="fp64", kappa=None, pre_sweeps=1, post_sweeps=1,
                  symmetric=True, max_rhs=0, check_every=1, persistent=False, fixed_point=True, pdl=True, block_fp=True,
-                 cluster_tail=False, restart_every=0, bfp_split=False, device=None):
-        self.lib = _lib.load()
+                 cluster_tail=False, restart_every=0, bfp_split=False, device=None, lib=None):
+        self.lib = lib if lib is not None else _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("HpcgProblem needs a CUDA device")
         self.device = torch.device(device or "cuda")
@@ -466,8 +466,8 @@ class HpcgSplit:
 class HpcgBatch:
     """A batch of independent grids (hpcg_setup_batch), vectors concatenated."""
 
-    def __init__(self, dims, levels=4, precision="fp64", device=None):
-        self.lib = _lib.load()
+    def __init__(self, dims, levels=4, precision="fp64", device=None, lib=None):
+        self.lib = lib if lib is not None else _lib.load()
         self.device = torch.device(device or "cuda")
         flat = [int(v) for d in dims for v in d]
         self.count = len(dims)

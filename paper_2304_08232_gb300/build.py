@@ -33,16 +33,17 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra=()):
+def build(force=False, verbose=False, extra=(), out_dir=None, lib_name=None):
     nvcc = os.environ.get("NVCC", "nvcc")
-    os.makedirs(OUT_DIR, exist_ok=True)
+    out_dir = out_dir or OUT_DIR
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "hpcg.h"))
     srcs = sources()
     objs = []
     procs = []
     for src in srcs:
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers + [os.path.abspath(__file__)]):
             cmd = [nvcc] + ARCH + FLAGS + list(extra) + ["-c", src, "-o", obj]
@@ -58,7 +59,7 @@ def build(force=False, verbose=False, extra=()):
             failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed for: %s" % ", ".join(failed))
-    out = lib_path()
+    out = os.path.join(out_dir, lib_name or LIB_NAME)
     if force or _stale(out, objs):
         tmp = out + ".tmp%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
@@ -67,6 +68,14 @@ def build(force=False, verbose=False, extra=()):
         subprocess.check_call(cmd)
         os.replace(tmp, out)
     return out
+
+
+def build_checked(force=False, verbose=False):
+    """The bounds-checking build (-DHPCG_BOUNDS_CHECK) into its own folder:
+    every index range the default FP64 path touches is checked against its
+    array's extent, a miss recorded and skipped (hpcg_bounds_status)."""
+    return build(force=force, verbose=verbose, extra=("-DHPCG_BOUNDS_CHECK",), out_dir=os.path.join(HERE, "_build_bc"),
+                 lib_name="libhpcg_gb300_bc.so")
 
 
 if __name__ == "__main__":

@@ -78,10 +78,17 @@ __device__ __forceinline__ void ld_pairs_d(const double *__restrict__ line, int 
 
 // Sum over lines y-1, y, y+1 of plane zz (those with ok set), at the largest
 // exponent of the three; returns that exponent.
+// nrows, nlines: the instance's rows and x-lines (the extents the
+// bounds-checking build checks the three lines against).
 template <int NC, bool COH = false>
 __device__ __forceinline__ int bfp_plane_sum(const long long *__restrict__ qg, const int *__restrict__ eg, int nx, int ny, long sxy, int y,
-                                             int zz, bool oka, bool okb, bool okd, int lane, long long (&te)[NC], long long (&to)[NC]) {
+                                             int zz, bool oka, bool okb, bool okd, int lane, long long (&te)[NC], long long (&to)[NC],
+                                             long nrows, long nlines) {
   const long li = (long)zz * ny + y;
+  const long row0 = (long)zz * sxy + (long)(y - 1) * nx;
+  oka = oka && HPCG_IN(li - 1, 1, 0, nlines) && HPCG_IN(row0, nx, 0, nrows);
+  okb = okb && HPCG_IN(li, 1, 0, nlines) && HPCG_IN(row0 + nx, nx, 0, nrows);
+  okd = okd && HPCG_IN(li + 1, 1, 0, nlines) && HPCG_IN(row0 + 2 * nx, nx, 0, nrows);
   const int ea = oka ? ld_line<COH>(eg + li - 1) : kFxMinE;
   const int eb = okb ? ld_line<COH>(eg + li) : kFxMinE;
   const int ed = okd ? ld_line<COH>(eg + li + 1) : kFxMinE;
@@ -97,6 +104,11 @@ __device__ __forceinline__ int bfp_plane_sum(const long long *__restrict__ qg, c
     to[c] = (shr_q(ao[c], et - ea) + shr_q(bo[c], et - eb)) + shr_q(d_o[c], et - ed);
   }
   return et;
+}
+
+// First row of coarse line (y/2, zz/2) of coarse instance table entry gc.
+__device__ __forceinline__ long gc_base_of(const Inst &gc, int zz, int y) {
+  return gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
 }
 
 // New value of a colour step from its exact sum t (scale S), stored at scale
@@ -163,7 +175,7 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
     const int zz = 2 * m0 + pz - 1;
     const bool zin = zz >= 0;
     Ec = bfp_plane_sum<NC, COH>(qg, eg, nx, ny, sxy, y, zz, zin && y - 1 >= 0 && vyo, zin && vy0, zin && y + 1 < ny && vyo, lane, tpe,
-                                tpo);
+                                tpo, g.n, (long)ny * nz);
   }
   if (done) return;  // converged instance: nothing changes
   for (int m = m0; m < m1; ++m) {
@@ -171,15 +183,20 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
     const bool zin = zz + 1 < nz;
     long long te[NC], to[NC];
     const int et = bfp_plane_sum<NC, COH>(qg, eg, nx, ny, sxy, y, zz + 1, zin && y - 1 >= 0 && vyo, zin && vy0, zin && y + 1 < ny && vyo,
-                                          lane, te, to);
+                                          lane, te, to, g.n, (long)ny * nz);
     const long li = (long)zz * ny + y;
     const long rowbase = (long)zz * sxy + (long)y * nx;
-    const int eu = ym ? ld_line<COH>(eg + li - 1) : kFxMinE;
-    const int ew = yp ? ld_line<COH>(eg + li + 1) : kFxMinE;
+    // the own line (z, r, the FP64 copy, kappa fields, its exponent and r.z
+    // partial) and the lines beside it, against the instance's extents
+    if (!(HPCG_IN(rowbase, nx, 0, g.n) && HPCG_IN(li, 1, 0, (long)ny * nz))) continue;
+    const bool ymc = ym && HPCG_IN(rowbase - nx, nx, 0, g.n) && HPCG_IN(li - 1, 1, 0, (long)ny * nz);
+    const bool ypc = yp && HPCG_IN(rowbase + nx, nx, 0, g.n) && HPCG_IN(li + 1, 1, 0, (long)ny * nz);
+    const int eu = ymc ? ld_line<COH>(eg + li - 1) : kFxMinE;
+    const int ew = ypc ? ld_line<COH>(eg + li + 1) : kFxMinE;
     int eo = own_valid ? (COH ? __ldcg(eg + li) : eg[li]) : kFxMinE;
     long long ue[NC], uo[NC], we[NC], wo[NC], qe[NC], qo[NC];
-    ld_pairs_q<NC, COH>(qg + rowbase - nx, ym, nx, lane, ue, uo);
-    ld_pairs_q<NC, COH>(qg + rowbase + nx, yp, nx, lane, we, wo);
+    ld_pairs_q<NC, COH>(qg + rowbase - nx, ymc, nx, lane, ue, uo);
+    ld_pairs_q<NC, COH>(qg + rowbase + nx, ypc, nx, lane, we, wo);
     if (own_valid && COH) {
       ld_pairs_q<NC, true>(qg + rowbase, true, nx, lane, qe, qo);
     } else {
@@ -198,6 +215,9 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
       // (the arithmetic of prolong_bfp_line, in registers)
       const Inst gc = tabcp[ii];
       const long lic = (long)(zz >> 1) * gc.ny + (y >> 1);
+      if (!(HPCG_IN(gc.off + lic * gc.nx, (nx + 1) / 2, gc.off, gc.off + gc.n) &&
+            HPCG_IN(gc.poff + lic, 1, gc.poff, gc.poff + (long)gc.ny * gc.nz)))
+        continue;
       const int e_c = ld_line<COH>(zec + gc.poff + lic);
       const int Sp = max(eo, e_c) + 1;
 #pragma unroll
@@ -278,9 +298,11 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
       if (rc) {
         const Inst gc = tabc[ii];
         const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
+        if (HPCG_IN(cbase, (nx + 1) / 2, gc.off, gc.off + gc.n)) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-          if (64 * c + 2 * lane < nx) rc[cbase + 32 * c + lane] = bfp_nan();
+          for (int c = 0; c < NC; ++c)
+            if (64 * c + 2 * lane < nx) rc[cbase + 32 * c + lane] = bfp_nan();
+        }
       }
       continue;
     }
@@ -352,7 +374,8 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
       for (int o = 16; o > 0; o >>= 1) rz += __shfl_down_sync(kFull, rz, o);
       if (lane == 0) dpart[g.poff + li] = rz;
     }
-    if (rc) {  // r - A z at the even points from the final values, exactly
+    if (rc && HPCG_IN(gc_base_of(tabc[ii], zz, y), (nx + 1) / 2, tabc[ii].off, tabc[ii].off + tabc[ii].n)) {
+      // r - A z at the even points from the final values, exactly
       const Inst gc = tabc[ii];
       const long cbase = gc.off + (long)(zz >> 1) * gc.nx * gc.ny + (long)(y >> 1) * gc.nx;
       prev_of_i<NC>(oO, nb, lane);

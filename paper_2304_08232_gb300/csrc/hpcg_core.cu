@@ -1940,6 +1940,27 @@ const char *hpcg_strerror(int status) {
 }
 
 const char *hpcg_last_cuda_error(void) { return g_last_cuda_error; }
+
+int hpcg_bounds_status(long long *count_host, long long *first_host, int reset) {
+  if (!count_host || !first_host) return HPCG_ERR_INVALID_ARG;
+#ifdef HPCG_BOUNDS_CHECK
+  BoundsWord w;
+  CK(cudaMemcpyFromSymbol(&w, g_bounds, sizeof(w)));
+  *count_host = (long long)w.count;
+  first_host[0] = w.first ? (long long)((w.first - 1) >> 40) : -1;                 // source line of the first violation
+  first_host[1] = w.first ? (long long)((w.first - 1) & ((1ULL << 40) - 1)) : -1;  // its index (low 40 bits)
+  if (reset) {
+    const BoundsWord zero = {0, 0};
+    CK(cudaMemcpyToSymbol(g_bounds, &zero, sizeof(zero)));
+  }
+  return HPCG_OK;
+#else
+  (void)reset;
+  *count_host = 0;
+  first_host[0] = first_host[1] = -1;
+  return HPCG_ERR_UNSUPPORTED;
+#endif
+}
 long hpcg_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"

@@ -6,6 +6,34 @@
 
 namespace hpcg {
 
+// Bounds-checking build (compiled with -DHPCG_BOUNDS_CHECK): before each group
+// of global accesses, the kernels of the default FP64 path check the index
+// range they are about to touch against the extent of its array (an
+// instance's rows, its x-lines, the next level's rows), and on a miss count
+// the violation, remember the first one (source line and index) in a device
+// word and skip the access; nothing traps.  hpcg_bounds_status reads the
+// word.  In the normal build HPCG_IN is the constant true and every check
+// compiles away.
+#ifdef HPCG_BOUNDS_CHECK
+struct BoundsWord {
+  unsigned long long count;
+  unsigned long long first;  // (source line << 40) | (index & (2^40 - 1)), + 1 so that 0 means none
+};
+static __device__ BoundsWord g_bounds;  // one per translation unit (the kernels of hpcg_core.cu use this one)
+static __device__ __noinline__ bool bounds_fail(long first, int line) {
+  atomicAdd(&g_bounds.count, 1ULL);
+  atomicCAS(&g_bounds.first, 0ULL, (((unsigned long long)line << 40) | ((unsigned long long)first & ((1ULL << 40) - 1))) + 1ULL);
+  return false;
+}
+// [first, first + len) inside [lo, hi)?
+static __device__ __forceinline__ bool bounds_ok(long first, long len, long lo, long hi, int line) {
+  return (first >= lo && first + len <= hi) ? true : bounds_fail(first, line);
+}
+#define HPCG_IN(first, len, lo, hi) ::hpcg::bounds_ok((long)(first), (long)(len), (long)(lo), (long)(hi), __LINE__)
+#else
+#define HPCG_IN(first, len, lo, hi) true
+#endif
+
 // Programmatic dependent launch: wait until the preceding kernel has finished
 // and its writes are visible.  Blocks signal their dependents implicitly when
 // they exit, so the next kernel is launched as this one drains instead of

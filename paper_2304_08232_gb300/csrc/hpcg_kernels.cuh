@@ -195,6 +195,13 @@ __global__ void k_convert(const Inst *__restrict__ tab, int count, const Tin *__
 // a fixed strided subset, blocks reduce by a fixed tree, and the final sum over
 // block partials runs in a fixed order.
 
+// Rows and x-lines of a level over all instances (the extents the
+// bounds-checking build checks vector and partial indices against).
+__device__ __forceinline__ long level_rows(const Inst *__restrict__ tab, int count) { return tab[count - 1].off + tab[count - 1].n; }
+__device__ __forceinline__ long level_lines(const Inst *__restrict__ tab, int count) {
+  return tab[count - 1].poff + (long)tab[count - 1].ny * tab[count - 1].nz;
+}
+
 // partials[b] = sum over this block's subset of a_i * b_i (b in FP64, or the
 // FP32 output of the mixed-precision preconditioner, widened exactly)
 template <typename TB>
@@ -210,7 +217,8 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const Inst *__restr
   if (!(st && st[ii].done)) {
     const long stride = (long)g.nred * kRedThreads;
     #pragma unroll 4
-    for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) s += a[g.off + i] * (double)bv[g.off + i];
+    for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride)
+      if (HPCG_IN(g.off + i, 1, 0, level_rows(tab, count))) s += a[g.off + i] * (double)bv[g.off + i];
   }
   s = block_sum(s, sh);
   if (threadIdx.x == 0) partials[blk] = s;
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize_lines(const Inst *__re
   const int cnt = g.ny * g.nz;
   const int per = (cnt + kFinCluster - 1) / kFinCluster;
   const int lo = min(cnt, k * per), hi = min(cnt, lo + per);
-  const double s = done ? 0.0 : sum_partials(partials, g.poff + lo, hi - lo, sh);
+  const double s = (done || !HPCG_IN(g.poff + lo, hi - lo, 0, level_lines(tab, count))) ? 0.0 : sum_partials(partials, g.poff + lo, hi - lo, sh);
   if (threadIdx.x == 0) slice_sum = s;
   cluster.sync();
   if (k == 0 && threadIdx.x == 0 && !done) {
@@ -313,6 +321,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(const Inst *__restrict
   #pragma unroll 4
   for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
     const long gi = g.off + i;
+    if (!HPCG_IN(gi, 1, 0, level_rows(tab, count))) continue;
     const double zi = (double)zv[gi];
     if (upd_x) {
       const double po = p[gi];
@@ -339,6 +348,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_x_restart(const Inst *__
   #pragma unroll 4
   for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
     const long gi = g.off + i;
+    if (!HPCG_IN(gi, 1, 0, level_rows(tab, count))) continue;
     x[gi] = x[gi] + alpha * p[gi];
   }
 }
@@ -358,6 +368,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_x_pending(const Inst *__
   #pragma unroll 4
   for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
     const long gi = g.off + i;
+    if (!HPCG_IN(gi, 1, 0, level_rows(tab, count))) continue;
     x[gi] = x[gi] + alpha * p[gi];
   }
 }
@@ -380,6 +391,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(const Inst *__restric
     #pragma unroll 4
     for (long i = (long)(blk - g.blk_red) * kRedThreads + threadIdx.x; i < g.n; i += stride) {
       const long gi = g.off + i;
+      if (!HPCG_IN(gi, 1, 0, level_rows(tab, count))) continue;
       if (x) x[gi] = x[gi] + alpha * p[gi];
       const double rn = r[gi] - alpha * ap[gi];
       r[gi] = rn;

@@ -61,7 +61,7 @@ __device__ __forceinline__ void cp_async_wait() {
 template <int NC>
 __device__ __forceinline__ void spmv_fetch_line(const double *__restrict__ xg, int nx, int ny, int nz, long sxy, int zp, int yl, int lane,
                                                 bool vec16, long long *__restrict__ slot) {
-  if (zp < 0 || zp >= nz || yl < 0 || yl >= ny) {
+  if (zp < 0 || zp >= nz || yl < 0 || yl >= ny || !HPCG_IN((long)zp * sxy + (long)yl * nx, nx, 0, (long)nz * sxy)) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) slot[lane + 32 * c] = 0;
     return;
@@ -182,6 +182,7 @@ __device__ __forceinline__ void spmv_stage_block(const Inst *__restrict__ tab, i
   // line's partial of x . y
   auto emit = [&](int zz, double (&ax)[NC]) {
     const long rowbase = (long)zz * sxy + (long)yy * nx;
+    if (!(HPCG_IN(rowbase, nx, 0, g.n) && HPCG_IN((long)zz * ny + yy, 1, 0, (long)ny * nz))) return;  // the whole warp
     double dotv = 0.0;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -206,6 +207,7 @@ __device__ __forceinline__ void spmv_stage_block(const Inst *__restrict__ tab, i
     cp_async_wait<0>();
     if (!own) return;
     for (int zz = zfrom; zz < z1; ++zz) {
+      if (!HPCG_IN((long)zz * sxy + (long)yy * nx, nx, 0, g.n)) continue;
       double t0[NC], t1[NC], t2[NC], u[NC], ul[NC], ur[NC], ax[NC];
       tsum<double, NC>(xg, nx, ny, nz, yy, zz - 1, lane, t0);
       tsum<double, NC>(xg, nx, ny, nz, yy, zz, lane, t1);
@@ -246,7 +248,7 @@ __device__ __forceinline__ void spmv_stage_block(const Inst *__restrict__ tab, i
     if (__syncthreads_or(convert(bn))) return fp64_rows(zz);
     long long T2[NC];
     const int e2 = spmv_plane_sum<NC>(sq + bn * bstride, se + bn * nslot, w, lane, T2);
-    if (own) {
+    if (own && HPCG_IN((long)zz * sxy + (long)yy * nx, nx, 0, g.n)) {  // kappa and x are read at the own row
       const int E = max(max(e0, e1), e2);
       long long u[NC], ul[NC], ur[NC];
 #pragma unroll
