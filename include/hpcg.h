@@ -350,6 +350,14 @@ int hpcg_persistent_levels(hpcg_handle h, int *first_level);
  * hpcg_setup; NO_WORKSPACE beyond the size limit; CUDA for a failed launch. */
 #define HPCG_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const double *r_dev, double *z_dev, void *stream);
+/* For checking the allocation-free V-cycle's coarse levels (no counterpart in
+ * the paper either): copies r_l and z_l (FP64, (nx>>l)(ny>>l)(nz>>l) values,
+ * either pointer may be NULL) of coarse level `level` (1..levels-1) as the
+ * last hpcg_mg_vcycle_noalloc on the same hierarchy left them in the shared
+ * array, with device-to-device copies on `stream`; allocates nothing.
+ * Errors: INVALID_ARG for the size rules, a level out of range or two null
+ * pointers; NO_WORKSPACE beyond the array's size. */
+int hpcg_noalloc_level_vectors(int nx, int ny, int nz, int levels, int level, double *r_dev, double *z_dev, void *stream);
 
 /* --- materialised operator, rows grouped by colour (P^T A P) --------------------- */
 /* Section III-A: rows of one colour can be stored contiguously by permuting the

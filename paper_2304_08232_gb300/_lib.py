@@ -58,6 +58,7 @@ SIGNATURES = {
     "hpcg_batch_offsets": (_i, [_vp, ctypes.POINTER(_l)]),
     "hpcg_pcg_solve_batch": (_i, [_vp, _vp, _vp, _i, _d, ctypes.POINTER(hpcg_stats), _vp]),
     "hpcg_mg_vcycle_noalloc": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
+    "hpcg_noalloc_level_vectors": (_i, [_i, _i, _i, _i, _i, _vp, _vp, _vp]),
     "hpcg_autotune": (_i, [_vp, ctypes.POINTER(_i), _vp]),
     "hpcg_set_launch_shapes": (_i, [_vp, ctypes.POINTER(_i)]),
     "hpcg_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),

@@ -2020,13 +2020,10 @@ __global__ void k_noalloc_tables(int nx, int ny, int nz, int levels, Inst *__res
   }
 }
 
-extern "C" int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const double *r_dev, double *z_dev, void *stream) {
-  if (!r_dev || !z_dev || r_dev == z_dev) return HPCG_ERR_INVALID_ARG;
-  TRY(validate_dims(nx, ny, nz, levels));
-  // scratch layout: level tables, then r_l and z_l of every coarse level
-  const size_t tab_bytes = align256(sizeof(Inst) * kMaxLevels);
-  size_t need = tab_bytes;
-  size_t off_r[kMaxLevels] = {0}, off_z[kMaxLevels] = {0};
+// The array's layout for one hierarchy: the level tables, then r_l and z_l of
+// every coarse level (byte offsets); returns the bytes used.
+static size_t noalloc_layout(int nx, int ny, int nz, int levels, size_t *off_r, size_t *off_z) {
+  size_t need = align256(sizeof(Inst) * kMaxLevels);
   for (int l = 1; l < levels; ++l) {
     const size_t nl = (size_t)(nx >> l) * (size_t)(ny >> l) * (size_t)(nz >> l);
     off_r[l] = need;
@@ -2034,6 +2031,14 @@ extern "C" int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const 
     off_z[l] = need;
     need = align256(need + sizeof(double) * nl);
   }
+  return need;
+}
+
+extern "C" int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const double *r_dev, double *z_dev, void *stream) {
+  if (!r_dev || !z_dev || r_dev == z_dev) return HPCG_ERR_INVALID_ARG;
+  TRY(validate_dims(nx, ny, nz, levels));
+  size_t off_r[kMaxLevels] = {0}, off_z[kMaxLevels] = {0};
+  const size_t need = noalloc_layout(nx, ny, nz, levels, off_r, off_z);
   if (need > (size_t)HPCG_NOALLOC_SCRATCH_BYTES) return HPCG_ERR_NO_WORKSPACE;
   void *base_v = nullptr;
   TRY(noalloc_base(&base_v));
@@ -2075,5 +2080,23 @@ extern "C" int hpcg_mg_vcycle_noalloc(int nx, int ny, int nz, int levels, const 
       CKL("k_gs_color");
     }
   }
+  return HPCG_OK;
+}
+
+// Copies r_l and z_l of coarse level `level` of the last allocation-free
+// V-cycle on an nx x ny x nz hierarchy out of the array (device-to-device
+// copies on `stream`, nothing allocated); for checking the coarse levels.
+extern "C" int hpcg_noalloc_level_vectors(int nx, int ny, int nz, int levels, int level, double *r_dev, double *z_dev, void *stream) {
+  TRY(validate_dims(nx, ny, nz, levels));
+  if (level < 1 || level >= levels || (!r_dev && !z_dev)) return HPCG_ERR_INVALID_ARG;
+  size_t off_r[kMaxLevels] = {0}, off_z[kMaxLevels] = {0};
+  if (noalloc_layout(nx, ny, nz, levels, off_r, off_z) > (size_t)HPCG_NOALLOC_SCRATCH_BYTES) return HPCG_ERR_NO_WORKSPACE;
+  void *base_v = nullptr;
+  TRY(noalloc_base(&base_v));
+  const char *base = (const char *)base_v;
+  const size_t bytes = sizeof(double) * (size_t)(nx >> level) * (size_t)(ny >> level) * (size_t)(nz >> level);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (r_dev) CK(cudaMemcpyAsync(r_dev, base + off_r[level], bytes, cudaMemcpyDeviceToDevice, s));
+  if (z_dev) CK(cudaMemcpyAsync(z_dev, base + off_z[level], bytes, cudaMemcpyDeviceToDevice, s));
   return HPCG_OK;
 }
