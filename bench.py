@@ -34,11 +34,10 @@ HBM_FALLBACK_GBS = 6800.0
 L2_BYTES = 135528448
 # the metric both arms report (the GPU solve, and --impl reference: the CPU oracle)
 METRIC = "HPCG-rule GFLOP/s + HBM GB/s at 192^3; mixed vs FP64 time to 1e-9 residual"
-# FP64-pipe warp instructions of one FP64 CG iteration per finest-level row, from
-# one ncu capture of an iteration's kernels (sm__inst_executed_pipe_fp64.sum,
-# profiles/fp64_instructions_per_iteration.md); every level's work scales
-# with the finest level's rows.
-FP64_WARP_INSTR_PER_ROW_ITER = 0.3495
+# FP64-pipe warp instructions of one FP64 CG iteration per finest-level row at
+# 192^3, from one ncu count of an iteration's kernels
+# (sm__inst_executed_pipe_fp64.sum, profiles/fp64_instructions_per_iteration.md).
+FP64_WARP_INSTR_PER_ROW_ITER = 0.2203
 
 
 def bench_config(world=1):
@@ -598,9 +597,10 @@ def run_gpu(args):
     # ncu's DRAM bytes confirm (traffic).
     bytes_launch = 107 * n / launches_l0
     achieved_gbs = bytes_launch / (k_ms * 1e-3) / 1e9
-    # DRAM traffic of one finest-level launch (post-smoother run [0,1]) from an
-    # ncu capture at 192^3 (profiles/k_gs_lines_bfp_192cubed.md)
-    traffic = (71.048192e6 + 0.411392e6) if (NX, NY, NZ) == (192, 192, 192) else None
+    # DRAM bytes (read + write) per finest-level launch, averaged over the 14
+    # launches of one V-cycle, from an ncu capture at 192^3
+    # (profiles/k_gs_lines_bfp_192cubed.md)
+    traffic = 61.76e6 if (NX, NY, NZ) == (192, 192, 192) else None
     roofline = {"bound": "hbm", "kernel": "k_gs_lines_bfp<3> (finest level, colour-pair runs of the V-cycle)",
                 "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
                 "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
@@ -631,22 +631,26 @@ def run_gpu(args):
                                        "achieved_gbs": 12 * n / (sweep_ms / 7 * 1e-3) / 1e9,
                                        "fp64_instr_per_updated_row": 4}
     del r, z
-    # SpMV line kernel (secondary): 7 + 4/zc FP64 instructions per row
-    zr = shapes[0][1]
+    # the SpMV alone (y = A x, no partials): x and y together fit L2 at 192^3,
+    # so L2 is flushed (a 256 MB write) before every timed launch; median of 10
     xs_ = torch.randn(n, dtype=torch.float64, device=dev)
     ys_ = torch.empty_like(xs_)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)
     for _ in range(3):
         prob.spmv(xs_, out=ys_)
-    torch.cuda.synchronize()
-    k0.record(stream)
-    for _ in range(reps):
+    sp_times = []
+    for _ in range(10):
+        flush.zero_()
+        k0.record(stream)
         prob.spmv(xs_, out=ys_)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    sp_ms = k0.elapsed_time(k1) / reps
+        k1.record(stream)
+        torch.cuda.synchronize()
+        sp_times.append(k0.elapsed_time(k1))
+    sp_ms = sorted(sp_times)[5]
+    del flush
     # k_spmv_stage_fx: the 27-point box sum in fixed point from lines staged in
     # shared memory; no FP64 instruction without the p.Ap partials
-    spmv = {"kernel": "k_spmv_stage_fx<6,0>", "ms": sp_ms, "fp64_instr_per_row": 0,
+    spmv = {"kernel": "k_spmv_stage_fx<6,0>", "ms": sp_ms, "fp64_instr_per_row": 0, "timing": "L2 flushed before each launch, median of 10",
             "g_fp64_instr_s": n * 1 / (sp_ms * 1e-3) / 1e9,
             "hbm_gbs_algorithmic": 16 * n / (sp_ms * 1e-3) / 1e9,
             "hbm_frac_of_measured": 16 * n / (sp_ms * 1e-3) / 1e9 / measured_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS)}

@@ -369,9 +369,8 @@ __device__ __forceinline__ void gs_bfp_block(int blk, int wy, const Inst *__rest
       }
     }
     if (lane == 0) eg[li] = sout - up;
-    if (zout && dpart) {  // per-line partial of r.z, fixed shuffle tree
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) rz += __shfl_down_sync(kFull, rz, o);
+    if (zout && dpart) {  // per-line partial of r.z, exact tree on the integer pipe
+      rz = warp_sum_fx(rz);
       if (lane == 0) dpart[g.poff + li] = rz;
     }
     if (rc && HPCG_IN(gc_base_of(tabc[ii], zz, y), (nx + 1) / 2, tabc[ii].off, tabc[ii].off + tabc[ii].n)) {

@@ -69,6 +69,29 @@ __device__ __forceinline__ int warp_max(int v) {
   return v;
 }
 
+// Sum of one FP64 value per lane of a warp (the per-line partials of r.z and
+// p.Ap), valid in lane 0, on the integer pipe: every value in fixed point at
+// the warp's largest biased exponent E (|q| < 2^58, 32 terms below 2^63), an
+// exact int64 tree, one rounding.  Each term loses under 2^-58 of the largest
+// value, as close as an FP64 tree gets, and the result does not depend on
+// the order of the additions.  It keeps the five FP64 adds per line off the
+// narrow FP64 pipe (one FP64 CG iteration at 192^3: 1.56 M FP64-pipe warp
+// instructions instead of about 1.75 M).  A warp holding huge or non-finite
+// values (E > kFxMaxE) sums in FP64, so NaN and Inf propagate.
+__device__ __forceinline__ double warp_sum_fx(double v) {
+  const int e = warp_max(fx_exp(v));
+  if (e > kFxMaxE) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+  }
+  const int E = max(e, kFxMinE);
+  long long q = fx_of(v, E);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(kFull, q, o);
+  return fx_to_double(q, E);
+}
+
 template <int NC>
 __device__ __forceinline__ void prev_of_i(const long long (&v)[NC], long long (&out)[NC], int lane) {
 #pragma unroll

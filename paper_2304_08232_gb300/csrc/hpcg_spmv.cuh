@@ -194,9 +194,8 @@ __device__ __forceinline__ void spmv_stage_block(const Inst *__restrict__ tab, i
         if (partials) dotv += xg[rowbase + xx] * out;
       }
     }
-    if (partials) {  // fixed shuffle tree over the lanes of this line
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dotv += __shfl_down_sync(kFull, dotv, o);
+    if (partials) {  // exact tree over the lanes of this line, on the integer pipe
+      dotv = warp_sum_fx(dotv);
       if (lane == 0) partials[g.poff + (long)zz * ny + yy] = dotv;
     }
   };
