@@ -23,7 +23,8 @@ V-cycle's own launches, fusions included) and hpcg_get/set_level_vectors:
   level l fed the GPU's own r_l, and each r_l is the restricted residual of
   the level above.
 Every storage form is covered: block floating point (the default), FP64 z,
-mixed precision, and the single-launch coarse ends (cluster_tail, persistent).
+mixed precision, the single-launch coarse ends (cluster_tail, persistent) and
+the line split over warps (bfp_split).
 """
 import numpy as np
 import pytest
@@ -43,6 +44,7 @@ MODES = {
     "cluster": {"cluster_tail": True},
     "persistent": {"persistent": True},
     "persistent_mixed": {"persistent": True, "precision": "mixed"},
+    "bfp_split": {"bfp_split": True},  # lines of 65-256 points split over warps (96 x 64 x 80's finest level)
 }
 SHAPES = [((16, 16, 16), 4), ((64, 32, 48), 4), ((96, 64, 80), 4)]
 EPS64 = np.finfo(np.float64).eps
