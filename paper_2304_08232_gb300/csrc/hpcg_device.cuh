@@ -79,10 +79,82 @@ __device__ __forceinline__ T inv_diag_of(const T *__restrict__ invd, long gi) {
   return invd ? invd[gi] : T(1) / T(26);
 }
 
-// Deterministic block sum (fixed shuffle tree, fixed warp order); result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double *sh) {
+constexpr unsigned kFull = 0xffffffffu;
+
+// Exact 64-bit fixed point for sums of FP64 values (used by the line kernels
+// of hpcg_fixed.cuh, hpcg_bfp.cuh and hpcg_spmv.cuh, and by the reductions
+// below): q(v) = trunc(v * 2^(1080 - E)) for a value whose biased exponent is
+// at most E, so |q| < 2^58 and 32 such terms sum below 2^63 exactly.
+constexpr int kFxMinE = 64, kFxMaxE = 2000;
+
+__device__ __forceinline__ int fx_exp(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
+
+// q(v) for a value whose biased exponent is at most E (E in [kFxMinE, kFxMaxE]).
+__device__ __forceinline__ long long fx_of(double v, int E) {
+  const int hi = __double2hiint(v);
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int e = (hi >> 20) & 0x7FF;
+  const unsigned long long m = ((unsigned long long)((unsigned)(hi & 0xFFFFF) | 0x100000u) << 32) | lo;
+  unsigned long long q;
+  // |v| = m 2^(e-1075); q = m 2^(e-E+5) = (m << 5) >> (E - e); shifts of 64 or
+  // more give 0 (zeros and denormals have e = 0 and E >= 64)
+  asm("shr.b64 %0, %1, %2;" : "=l"(q) : "l"(m << 5), "r"((unsigned)(E - e)));
+  const long long s = (long long)(hi >> 31);
+  return ((long long)q ^ s) - s;
+}
+
+// q 2^(E-1080) as FP64, rounded to nearest (ties to even), built from the
+// bits of q on the integer pipe: an int64 -> double conversion instruction
+// occupies the FP64 pipe for several of its issue slots on this GPU.
+// E in [kFxMinE, kFxMaxE] keeps the result a normal number.
+__device__ __forceinline__ double fx_to_double(long long q, int E) {
+  const unsigned long long sign = (unsigned long long)q & 0x8000000000000000ULL;
+  const unsigned long long a = q < 0 ? 0ULL - (unsigned long long)q : (unsigned long long)q;  // |q| < 2^63
+  const int lz = __clzll(a);                                  // >= 1 for a != 0
+  const unsigned long long m = a << lz;                        // leading one at bit 63
+  const unsigned long long mant = m >> 11;                     // 53 significant bits
+  const unsigned long long rbit = (m >> 10) & 1ULL;            // first dropped bit
+  const unsigned long long sticky = (m & 0x3FFULL) != 0ULL;    // any further dropped bit
+  const unsigned long long up = rbit & (sticky | (mant & 1ULL));
+  // |value| = m 2^(E - 1080 - lz); biased exponent of the leading one: E + 6 - lz.
+  // A carry out of the mantissa rounding moves into the exponent field.
+  const unsigned long long bits = ((unsigned long long)(E + 6 - lz) << 52) + (mant - (1ULL << 52)) + up;
+  return a == 0ULL ? 0.0 : __longlong_as_double((long long)(bits | sign));
+}
+
+__device__ __forceinline__ int warp_max(int v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// Sum of one FP64 value per lane of a warp (the per-line partials of r.z and
+// p.Ap), valid in lane 0, on the integer pipe: every value in fixed point at
+// the warp's largest biased exponent E (|q| < 2^58, 32 terms below 2^63), an
+// exact int64 tree, one rounding.  Each term loses under 2^-58 of the largest
+// value, as close as an FP64 tree gets, and the result does not depend on
+// the order of the additions.  It keeps the five FP64 adds per line off the
+// narrow FP64 pipe (one FP64 CG iteration at 192^3: 1.56 M FP64-pipe warp
+// instructions instead of about 1.75 M).  A warp holding huge or non-finite
+// values (E > kFxMaxE) sums in FP64, so NaN and Inf propagate.
+__device__ __forceinline__ double warp_sum_fx(double v) {
+  const int e = warp_max(fx_exp(v));
+  if (e > kFxMaxE) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+  }
+  const int E = max(e, kFxMinE);
+  long long q = fx_of(v, E);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(kFull, q, o);
+  return fx_to_double(q, E);
+}
+
+// Deterministic block sum (exact integer tree over each warp's lanes, warps
+// added in a fixed order); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  v = warp_sum_fx(v);
   const int lane = threadIdx.x & 31;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int warp = tid >> 5;

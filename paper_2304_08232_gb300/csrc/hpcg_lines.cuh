@@ -23,7 +23,6 @@
 
 namespace hpcg {
 
-constexpr unsigned kFull = 0xffffffffu;
 
 // vl[c] = v at x-1, vr[c] = v at x+1, for x = lane + 32c; zero past both ends
 // of the 32*NCH window (values at x >= nx must already be zero).
