@@ -37,7 +37,7 @@ METRIC = "HPCG-rule GFLOP/s + HBM GB/s at 192^3; mixed vs FP64 time to 1e-9 resi
 # FP64-pipe warp instructions of one FP64 CG iteration per finest-level row at
 # 192^3, from one ncu count of an iteration's kernels
 # (sm__inst_executed_pipe_fp64.sum, profiles/fp64_instructions_per_iteration.md).
-FP64_WARP_INSTR_PER_ROW_ITER = 0.2203
+FP64_WARP_INSTR_PER_ROW_ITER = 0.2065
 
 
 def bench_config(world=1):
