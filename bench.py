@@ -785,8 +785,7 @@ def run_gpu(args):
         "iteration_breakdown": breakdown, "fp64_solve_variants": variants, "forms": forms, "hpcg_checks": checks,
         "materialised_ell": ell, "cpu_baseline_1thread": cpu1, "ms_per_step_spread": [min(step_ms), max(step_ms)],
     }
-    detail_path = args.detail or (os.path.join(ROOT, "gpurun_out", "bench_detail.json")
-                                  if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    detail_path = args.detail
     if detail_path:
         with open(detail_path, "w") as f:
             json.dump(detail, f, indent=1, default=float)
@@ -824,7 +823,7 @@ def run_gpu(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "cpu_baseline_1thread_gflops": r3(cpu1["value"]) if cpu1 else None,
-        "detail": os.path.relpath(detail_path, ROOT) if detail_path else None,
+        "detail": detail_path,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -849,7 +848,7 @@ def main():
                     help="run only the materialised-operator study (sliced-ELL, colour-sorted and natural order, two "
                          "sub-domains) at the grid size and print its JSON (profiling runs)")
     ap.add_argument("--detail", default=None,
-                    help="file for the full measurement record (default gpurun_out/bench_detail.json when that folder exists)")
+                    help="file for the full measurement record (forms, variants, breakdowns); none by default")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="after the timed steps, one solve of this many CG iterations between cudaProfilerStart and "
                          "cudaProfilerStop (for ncu --profile-from-start off)")
