@@ -1151,9 +1151,6 @@ static int enqueue_pcg_init(hpcg_ctx *h, const double *b, double *x, int max_ite
              (const CgState *)nullptr);
     CKL("k_convert");
   }
-  if (max_iters <= 0) {
-    // nothing to iterate: mark every instance done
-  }
   return HPCG_OK;
 }
 
