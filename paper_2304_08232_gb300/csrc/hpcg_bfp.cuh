@@ -113,12 +113,17 @@ __device__ __forceinline__ long gc_base_of(const Inst &gc, int zz, int y) {
 
 // New value of a colour step from its exact sum t (scale S), stored at scale
 // sout: t / 26 with four guard bits from the integer multiplier, rounded to
-// nearest at S - 3; with kappa, t * (1 / A_ii) in FP64 converted at sout.
+// nearest at S - 3 (8 t / 26 = 4 t / 13 is never halfway between integers,
+// so the nearest is unique); with kappa, t * (1 / A_ii) in FP64 converted at
+// sout.  |t| < 2^58 at S (the colour steps' scale bound), so t + 13 2^56 is
+// positive and one unsigned multiply-high divides it; that offset is exactly
+// 2^58 units at S - 3 (13 2^56 * 8/26), taken off the quotient.  (The offset
+// touches only the high word, as does 2^58.)
 __device__ __forceinline__ long long bfp_new_value(long long t, int S, int sout, const double *__restrict__ invd, long gi) {
   if (!invd) {
-    const unsigned long long a = t < 0 ? 0ULL - (unsigned long long)t : (unsigned long long)t;
-    const long long q = (long long)((__umul64hi(a, kDiv26) + 1ULL) >> 1);
-    return t < 0 ? -q : q;
+    constexpr unsigned long long kOff = 13ULL << 56, kOffQ = 1ULL << 58;
+    const unsigned long long u = (unsigned long long)t + kOff;
+    return (long long)(((__umul64hi(u, kDiv26) + 1ULL) >> 1) - kOffQ);
   }
   return fx_of(fx_to_double(t, S) * invd[gi], sout);
 }
