@@ -600,7 +600,7 @@ def run_gpu(args):
     # DRAM bytes (read + write) per finest-level launch, averaged over the 14
     # launches of one V-cycle, from an ncu capture at 192^3
     # (profiles/k_gs_lines_bfp_192cubed.md)
-    traffic = 61.76e6 if (NX, NY, NZ) == (192, 192, 192) else None
+    traffic = 61.75e6 if (NX, NY, NZ) == (192, 192, 192) else None
     roofline = {"bound": "hbm", "kernel": "k_gs_lines_bfp<3> (finest level, colour-pair runs of the V-cycle)",
                 "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
                 "peak_basis": "%s copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
