@@ -856,6 +856,9 @@ def main():
                     help="time this many V-cycles alone and print per-level times (profiling runs of the preconditioner)")
     ap.add_argument("--cluster-tail", action="store_true", help="with --vcycles: hpcg_options.cluster_tail")
     ap.add_argument("--persistent", action="store_true", help="with --vcycles: hpcg_options.persistent")
+    ap.add_argument("--size-sweep", default=None,
+                    help="semicolon-separated nx,ny,nz grids: time the 50-iteration FP64 solve on each and print one "
+                         "JSON line (how the rates change with problem size; the paper solves the largest that fits)")
     ap.add_argument("--quick", action="store_true",
                     help="time the FP64 solve only (no kernel roofline, mixed comparison, e2e or CPU baseline)")
     args = ap.parse_args()
@@ -869,7 +872,53 @@ def main():
         return run_ell_only()
     if args.vcycles > 0:
         return run_vcycles(args)
+    if args.size_sweep:
+        return run_size_sweep(args)
     return run_gpu(args)
+
+
+def run_size_sweep(args):
+    """The FP64 MG-PCG solve (50 iterations, 4 levels, b = A ones) on each grid
+    of --size-sweep: CUDA-event time of --steps solves after --warmup, the
+    HPCG-rule rate, the whole solve against the per-row byte model, and the
+    finest level's colour-pair runs against the method's 107 n bytes per
+    V-cycle (14 launches)."""
+    import torch
+    from paper_2304_08232_gb300 import HpcgProblem
+    dev = torch.device("cuda", 0)
+    peak = measured_peaks()[0].get("hbm_gbs", HBM_FALLBACK_GBS)
+    out = []
+    for spec in args.size_sweep.split(";"):
+        nx, ny, nz = (int(v) for v in spec.split(","))
+        prob = HpcgProblem(nx, ny, nz, levels=LEVELS, device=dev)
+        b = prob.get_rhs()
+        x = torch.zeros_like(b)
+        for _ in range(max(args.warmup, 1)):
+            prob.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            prob.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        n = nx * ny * nz
+        prof = prob.profile_iteration(b)
+        fine_ms = prof["smoother_ms"][0]
+        out.append({"grid": [nx, ny, nz], "rows": n, "ms_per_solve": round(ms, 3),
+                    "gflops": round(hpcg_flops_per_iter(nx, ny, nz, LEVELS) * ITERS / (ms * 1e-3) / 1e9, 1),
+                    "whole_solve_frac": round(whole_solve_roofline(algorithmic_bytes_per_iter(nx, ny, nz, LEVELS) * ITERS, ms,
+                                                                   peak)["frac"], 4),
+                    "finest_smoother_frac": round(107 * n / (fine_ms * 1e-3) / 1e9 / peak, 4),
+                    "iteration_ms": round(prof["total_ms"], 4) if "total_ms" in prof else None,
+                    "smoother_ms_per_level": [round(v, 4) for v in prof["smoother_ms"]],
+                    "max_abs_err_vs_ones": float((x - 1.0).abs().max())})
+        del prob, b, x
+        torch.cuda.empty_cache()
+    print(json.dumps({"size_sweep": out, "levels": LEVELS, "cg_iters": ITERS, "hbm_peak_gbs": peak}), flush=True)
+    return 0
 
 
 def run_vcycles(args):
