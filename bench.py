@@ -882,7 +882,9 @@ def run_size_sweep(args):
     of --size-sweep: CUDA-event time of --steps solves after --warmup, the
     HPCG-rule rate, the whole solve against the per-row byte model, and the
     finest level's colour-pair runs against the method's 107 n bytes per
-    V-cycle (14 launches)."""
+    V-cycle; with the colour-pair runs of one plane parity grouped into one
+    launch as the autotuner chooses (auto), never (per_run) and always
+    (grouped)."""
     import torch
     from paper_2304_08232_gb300 import HpcgProblem
     dev = torch.device("cuda", 0)
@@ -890,64 +892,38 @@ def run_size_sweep(args):
     out = []
     for spec in args.size_sweep.split(";"):
         nx, ny, nz = (int(v) for v in spec.split(","))
-        prob = HpcgProblem(nx, ny, nz, levels=LEVELS, device=dev)
-        b = prob.get_rhs()
-        x = torch.zeros_like(b)
-        for _ in range(max(args.warmup, 1)):
-            prob.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            prob.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
         n = nx * ny * nz
-        prof = prob.profile_iteration(b)
-        fine_ms = prof["smoother_ms"][0]
-        out.append({"grid": [nx, ny, nz], "rows": n, "ms_per_solve": round(ms, 3),
-                    "gflops": round(hpcg_flops_per_iter(nx, ny, nz, LEVELS) * ITERS / (ms * 1e-3) / 1e9, 1),
-                    "whole_solve_frac": round(whole_solve_roofline(algorithmic_bytes_per_iter(nx, ny, nz, LEVELS) * ITERS, ms,
-                                                                   peak)["frac"], 4),
-                    "finest_smoother_frac": round(107 * n / (fine_ms * 1e-3) / 1e9 / peak, 4),
-                    "iteration_ms": round(prof["total_ms"], 4) if "total_ms" in prof else None,
-                    "smoother_ms_per_level": [round(v, 4) for v in prof["smoother_ms"]],
-                    "max_abs_err_vs_ones": float((x - 1.0).abs().max())})
-        del prob, b, x
-        torch.cuda.empty_cache()
+        entry = {"grid": [nx, ny, nz], "rows": n}
+        for name, fuse in (("auto", 0), ("per_run", -1), ("grouped", 1)):
+            prob = HpcgProblem(nx, ny, nz, levels=LEVELS, fuse_planes=fuse, device=dev)
+            b = prob.get_rhs()
+            x = torch.zeros_like(b)
+            for _ in range(max(args.warmup, 1)):
+                prob.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                prob.pcg_solve(b, max_iters=ITERS, tol=0.0, out=x)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            prof = prob.profile_iteration(b)
+            fine_ms = prof["smoother_ms"][0]
+            entry[name] = {"ms_per_solve": round(ms, 3),
+                           "gflops": round(hpcg_flops_per_iter(nx, ny, nz, LEVELS) * ITERS / (ms * 1e-3) / 1e9, 1),
+                           "whole_solve_frac": round(whole_solve_roofline(algorithmic_bytes_per_iter(nx, ny, nz, LEVELS) * ITERS, ms,
+                                                                          peak)["frac"], 4),
+                           "finest_smoother_frac": round(107 * n / (fine_ms * 1e-3) / 1e9 / peak, 4),
+                           "iteration_ms": round(prof["total_ms"], 4),
+                           "smoother_ms_per_level": [round(v, 4) for v in prof["smoother_ms"]],
+                           "max_abs_err_vs_ones": float((x - 1.0).abs().max())}
+            del prob, b, x
+            torch.cuda.empty_cache()
+        out.append(entry)
+        print(json.dumps(entry), file=sys.stderr, flush=True)
     print(json.dumps({"size_sweep": out, "levels": LEVELS, "cg_iters": ITERS, "hbm_peak_gbs": peak}), flush=True)
-    return 0
-
-
-def run_vcycles(args):
-    """Profiling runs of the preconditioner alone: `--vcycles K` V-cycles
-    (z = M r, r ~ N(0,1)) on the grid, with the coarse-end options given,
-    timed with CUDA events; prints one JSON line with the per-level times of
-    one CG iteration (hpcg_profile_iteration) as well."""
-    import torch
-    from hpcg_inputs import normal
-    from paper_2304_08232_gb300 import HpcgProblem
-    dev = torch.device("cuda", 0)
-    prob = HpcgProblem(NX, NY, NZ, levels=LEVELS, precision=args.precision, cluster_tail=args.cluster_tail,
-                       persistent=args.persistent, device=dev)
-    r = torch.as_tensor(normal(NX * NY * NZ, 0), device=dev)
-    z = torch.empty_like(r)
-    for _ in range(3):
-        prob.mg_vcycle(r, out=z)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.vcycles):
-        prob.mg_vcycle(r, out=z)
-    e1.record()
-    torch.cuda.synchronize()
-    pr = prob.profile_iteration(prob.get_rhs())
-    print(json.dumps({"grid": [NX, NY, NZ], "cluster_tail": args.cluster_tail, "persistent": args.persistent,
-                      "precision": args.precision, "ms_per_vcycle": e0.elapsed_time(e1) / args.vcycles,
-                      "iteration_profile": pr}), flush=True)
     return 0
 
 

@@ -97,6 +97,13 @@ typedef struct {
                         with one warp per 64-point chunk of a line (neighbours across chunks through
                         shared memory; same z bits, r.z partials summed chunk by chunk); 0 (default):
                         one warp per line */
+  int fuse_planes;   /* with block_fp, one grid: the colour-pair runs of a smoother application whose
+                        line classes share their z parity ([0 1], [2 3 2], [1 0]) run in one launch,
+                        one block per plane of that parity and a block barrier between runs (same
+                        bits; the planes between are read once per group instead of once per run).
+                        0 (default): the autotuner times each level both ways and keeps the faster
+                        (one launch per run measured faster at every size from 128^3 to
+                        384 x 1024 x 1024); 1: always; -1: never */
 } hpcg_options;
 
 typedef struct {

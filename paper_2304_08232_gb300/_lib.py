@@ -18,7 +18,7 @@ class hpcg_options(ctypes.Structure):
     _fields_ = [("nx", _i), ("ny", _i), ("nz", _i), ("levels", _i), ("precision", _i), ("pre_sweeps", _i),
                 ("post_sweeps", _i), ("symmetric", _i), ("check_every", _i), ("max_rhs", _i), ("autotune", _i),
                 ("fixed_point", _i), ("pdl", _i), ("persistent", _i), ("block_fp", _i), ("cluster_tail", _i),
-                ("restart_every", _i), ("bfp_split", _i)]
+                ("restart_every", _i), ("bfp_split", _i), ("fuse_planes", _i)]
 
 
 class hpcg_stats(ctypes.Structure):

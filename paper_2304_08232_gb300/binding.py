@@ -59,7 +59,8 @@ class HpcgProblem:
 
     def __init__(self, nx, ny, nz, levels=4, precision="fp64", kappa=None, pre_sweeps=1, post_sweeps=1,
                  symmetric=True, max_rhs=0, check_every=1, persistent=False, fixed_point=True, pdl=True, block_fp=True,
-                 cluster_tail=False, restart_every=0, bfp_split=False, device=None, lib=None):
+                 cluster_tail=False, restart_every=0, bfp_split=False, fuse_planes=0, device=None,
+                 lib=None):
         self.lib = lib if lib is not None else _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("HpcgProblem needs a CUDA device")
@@ -79,6 +80,7 @@ class HpcgProblem:
         opt.cluster_tail = 1 if cluster_tail else 0
         opt.restart_every = int(restart_every)
         opt.bfp_split = 1 if bfp_split else 0
+        opt.fuse_planes = int(fuse_planes)
         self.dims = (nx, ny, nz)
         self.levels = levels
         self.precision = precision

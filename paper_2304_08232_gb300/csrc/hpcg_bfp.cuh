@@ -461,6 +461,54 @@ __global__ void __launch_bounds__(256) k_gs_lines_bfp_refine(const Inst *__restr
 }
 
 // ---------------------------------------------------------------------------
+// Consecutive colour-pair runs whose line classes share the z parity pz (a
+// symmetric sweep's runs in class order are [0 1], [2 3 2], [1 0]) in one
+// launch.  A run on class (py, pz) reads, besides its own lines, the lines
+// of the other y parity in its own planes and the lines of the planes
+// between (parity 1 - pz), which no run of the group writes; so one block
+// per plane of parity pz takes every line of that plane, run after run with
+// a block barrier between runs, and no block reads what another block of the
+// launch writes.  Each run is gs_bfp_block on virtual blocks of one plane
+// (zc = 1) with L2-coherent loads (the lines written by the run before, by
+// other warps of the block): the same arithmetic per line as one launch per
+// run, so the same bits.  It saves a launch per run and reads the planes of
+// parity 1 - pz once per group instead of once per run, but a block then
+// takes a whole plane (no plane sum carried along z, loads through L2 only,
+// one block per SM): one launch per run measured faster at every grid size,
+// and the autotuner keeps the faster form per level.
+struct PlaneRun {
+  int cls, pa, steps, refine;  // refine: the coarser level's z is refined into this (class (0,0)) run
+  double *rc;                  // fused residual + injection into the coarser level, or null
+  double *zout, *dpart;        // FP64 z and per-line r.z partials (a class's last run), or null
+};
+constexpr int kPlaneMaxRuns = 3;
+struct PlaneRuns {
+  PlaneRun run[kPlaneMaxRuns];
+  int nruns, vmask;  // vmask: line classes holding valid z before the first run
+};
+constexpr int kPlaneWarps = 16;  // warps (lines at a time) of a plane block
+
+template <int NC>
+__global__ void __launch_bounds__(32 * kPlaneWarps, 1)
+    k_gs_planes_bfp(const Inst *__restrict__ tab, int count, const PlaneRuns R, const double *__restrict__ r, long long *__restrict__ zq,
+                    int *__restrict__ ze, const double *__restrict__ invd, const CgState *__restrict__ st, const Inst *__restrict__ tabc,
+                    const double *__restrict__ kap, const long long *__restrict__ zqc, const int *__restrict__ zec,
+                    const Inst *__restrict__ tabcp, const Inst g1) {
+  pdl_enter();
+  const int nby = (half_up(g1.ny) + kPlaneWarps - 1) / kPlaneWarps;  // virtual blocks of kPlaneWarps lines per plane
+  int vmask = R.vmask;
+  for (int k = 0; k < R.nruns; ++k) {
+    const PlaneRun &u = R.run[k];
+    for (int yb = 0; yb < nby; ++yb)
+      gs_bfp_block<NC, true>((int)blockIdx.x * nby + yb, threadIdx.y, tab, g1, count, kPlaneWarps, 1, u.cls & 1, (u.cls >> 1) & 1, u.pa,
+                             u.steps, vmask, r, zq, ze, invd, st, u.rc ? tabc : nullptr, u.rc, kap, u.zout, u.dpart,
+                             u.refine ? zqc : nullptr, u.refine ? zec : nullptr, u.refine ? tabcp : nullptr);
+    vmask |= 1 << u.cls;
+    __syncthreads();  // this run's lines are written before the next run reads them
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The same colour-pair runs with each x-line split over W warps, one 64-point
 // chunk each (x in [64k, 64k + 64), the lane holding the pair x = 64k + 2 lane,
 // + 1).  One warp per line holds W pairs per lane (122 registers at W = 3: two

@@ -819,6 +819,35 @@ static int enqueue_line_steps_bfp(hpcg_ctx *h, int l, int py, int pz, int pa, in
   return HPCG_OK;
 }
 
+// Runs R (one z parity pz) of level l in one launch of k_gs_planes_bfp.
+static int enqueue_planes_bfp(hpcg_ctx *h, int l, int pz, const PlaneRuns &R, const double *r, cudaStream_t s, const CgState *st) {
+  const LevelData &L = h->lv[l];
+  const LevelData *C = l + 1 < h->levels ? &h->lv[l + 1] : nullptr;
+  const double *invd = invd_of<double>(L, h->has_kappa);
+  const double *kap = kap_of<double>(L, h->has_kappa);
+  const Inst &g = L.inst[0];
+  const dim3 grid((unsigned)((g.nz - pz + 1) / 2)), block(32, kPlaneWarps);
+  const Inst *tabc = C ? C->tab.inst : nullptr;
+  const long long *zqc = C ? (const long long *)C->zq : nullptr;
+  const int *zec = C ? (const int *)C->ze : nullptr;
+  switch (L.tab.nch2) {
+#define HPCG_PL_CASE(N) \
+  case N: launch_k(k_gs_planes_bfp<N>, grid, block, 0, s, L.tab.inst, h->count, R, r, L.zq, L.ze, invd, st, tabc, kap, zqc, zec, tabc, g); break;
+    HPCG_PL_CASE(1) HPCG_PL_CASE(2) HPCG_PL_CASE(3) HPCG_PL_CASE(4) HPCG_PL_CASE(5) HPCG_PL_CASE(6)
+#undef HPCG_PL_CASE
+    default: return HPCG_ERR_UNSUPPORTED;
+  }
+  CKL("k_gs_planes_bfp");
+  return HPCG_OK;
+}
+
+// Whether level l's block-floating-point runs may be grouped by plane parity.
+static bool planes_apply(const hpcg_ctx *h, int l) {
+  const LevelData &L = h->lv[l];
+  const bool split = h->opt.bfp_split && L.tab.nch2 >= 2 && L.tab.nch2 <= 4 && L.tab.line_lpc <= kBfpSplitMaxLines;
+  return h->use_bfp && h->count == 1 && !split && L.tab.nch2 >= 1 && L.tab.nch2 <= 6;
+}
+
 // One smoother application (`sweeps` symmetric sweeps) on level l, grouped
 // into runs as in enqueue_smoother.  rc (nullable): residual + injection
 // fused into the last run, which for the symmetric smoother is class (0,0)
@@ -838,6 +867,9 @@ static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps,
     i = j;
   }
   int vmask = from_zero ? 0 : 0xF;
+  const bool planes = h->lv[l].planes;
+  PlaneRuns group{};  // runs of one plane parity waiting for their launch (planes)
+  int group_pz = -1;
   for (size_t i = 0; i < runs.size(); ++i) {
     const int k = runs[i].first, steps = runs[i].second, cls = k >> 1;
     bool last_of_class = true;
@@ -847,10 +879,31 @@ static int enqueue_smoother_bfp(hpcg_ctx *h, int l, const double *r, int sweeps,
     if (steps < 2 || (rc_here && (cls != 0 || last_parity != 0))) return HPCG_ERR_UNSUPPORTED;
     const bool refine_here = refine && i == 0;
     if (refine_here && cls != 0) return HPCG_ERR_UNSUPPORTED;
-    TRY(enqueue_line_steps_bfp(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, s, st, vmask, rc_here, last_of_class ? zout : nullptr,
-                               last_of_class ? dpart : nullptr, refine_here ? &h->lv[l + 1] : nullptr));
+    if (planes) {
+      const int pz = (cls >> 1) & 1;
+      if (group.nruns > 0 && (pz != group_pz || group.nruns == kPlaneMaxRuns)) {
+        TRY(enqueue_planes_bfp(h, l, group_pz, group, r, s, st));
+        group = PlaneRuns{};
+      }
+      if (group.nruns == 0) {
+        group.vmask = vmask;
+        group_pz = pz;
+      }
+      PlaneRun &u = group.run[group.nruns++];
+      u.cls = cls;
+      u.pa = k & 1;
+      u.steps = steps;
+      u.refine = refine_here ? 1 : 0;
+      u.rc = rc_here;
+      u.zout = last_of_class ? zout : nullptr;
+      u.dpart = last_of_class ? dpart : nullptr;
+    } else {
+      TRY(enqueue_line_steps_bfp(h, l, cls & 1, (cls >> 1) & 1, k & 1, steps, r, s, st, vmask, rc_here, last_of_class ? zout : nullptr,
+                                 last_of_class ? dpart : nullptr, refine_here ? &h->lv[l + 1] : nullptr));
+    }
     vmask |= 1 << cls;
   }
+  if (planes && group.nruns > 0) TRY(enqueue_planes_bfp(h, l, group_pz, group, r, s, st));
   prof_mark(PK_SMOOTH, l);  // one event per smoother application: its runs keep their launch overlap
   return HPCG_OK;
 }
@@ -1406,6 +1459,30 @@ static int time_shape(hpcg_ctx *h, int l, bool rows, int lpc, int zc, cudaStream
   return HPCG_OK;
 }
 
+// One block-floating-point smoother application on level l (from z = 0, as
+// the pre-smoother), timed over a few repetitions.
+static int time_smoother_bfp(hpcg_ctx *h, int l, const double *r, cudaStream_t s, float *ms) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = HPCG_OK;
+  const int reps = 4;
+  for (int it = 0; it <= reps && rc == HPCG_OK; ++it) {
+    if (it == 1) cudaEventRecord(e0, s);
+    rc = enqueue_smoother_bfp(h, l, r, 1, s, nullptr, true, nullptr, nullptr);
+  }
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HPCG_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+  *ms = t / reps;
+  return HPCG_OK;
+}
+
 static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s) {
   static const int lpcs[] = {1, 2, 4, 8};
   static const int zcs[] = {1, 2, 4, 8, 16};
@@ -1446,6 +1523,14 @@ static int autotune_impl(hpcg_ctx *h, int *shapes, cudaStream_t s) {
       set_line_prefixes(L);
     }
     CK(cudaMemcpyAsync((void *)L.tab.inst, L.inst.data(), sizeof(Inst) * h->count, cudaMemcpyHostToDevice, s));
+    if (h->opt.fuse_planes == 0 && planes_apply(h, l)) {  // one smoother application with and without grouped runs
+      float ms[2] = {0.f, 0.f};
+      for (int fused = 0; fused < 2; ++fused) {
+        L.planes = fused != 0;
+        TRY(time_smoother_bfp(h, l, a, s, &ms[fused]));
+      }
+      L.planes = ms[1] < ms[0];
+    }
   }
   CK(cudaStreamSynchronize(s));
   // partial-sum buffers are sized by the largest launch: keep within them
@@ -1605,6 +1690,7 @@ int hpcg_options_default(hpcg_options *opt, int nx, int ny, int nz) {
   opt->cluster_tail = 0;
   opt->restart_every = 0;
   opt->bfp_split = 0;
+  opt->fuse_planes = 0;
   return HPCG_OK;
 }
 
@@ -1623,6 +1709,7 @@ static int make_handle(const hpcg_options *opt, const std::vector<int> &dims, in
     for (const Inst &g : h->lv[l].inst) bfp = bfp && (g.nx % 2) == 0;
   }
   h->use_bfp = bfp;
+  for (int l = 0; l < h->levels; ++l) h->lv[l].planes = opt->fuse_planes > 0 && planes_apply(h, l);
   *out = h;
   return HPCG_OK;
 }

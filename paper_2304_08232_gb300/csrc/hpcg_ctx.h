@@ -47,6 +47,7 @@ struct LevelData {
   size_t o_tab = 0, o_r = 0, o_z = 0, o_r32 = 0, o_z32 = 0, o_kap = 0, o_invd = 0, o_kap32 = 0, o_invd32 = 0, o_zq = 0, o_ze = 0;
   long nlines = 0;  // x-lines over all instances (sum of ny * nz)
   bool even_nx = false;  // every instance's lines have an even length (x pairs move as vectors)
+  bool planes = false;   // block-floating-point smoother runs grouped by plane parity (k_gs_planes_bfp)
   // device pointers (valid once a workspace is bound)
   double *r = nullptr, *z = nullptr, *kap = nullptr, *invd = nullptr;
   float *r32 = nullptr, *z32 = nullptr, *kap32 = nullptr, *invd32 = nullptr;

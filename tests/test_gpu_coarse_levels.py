@@ -45,6 +45,7 @@ MODES = {
     "persistent": {"persistent": True},
     "persistent_mixed": {"persistent": True, "precision": "mixed"},
     "bfp_split": {"bfp_split": True},  # lines of 65-256 points split over warps (96 x 64 x 80's finest level)
+    "planes": {"fuse_planes": 1},  # the runs of one plane parity in one launch (k_gs_planes_bfp)
 }
 SHAPES = [((16, 16, 16), 4), ((64, 32, 48), 4), ((96, 64, 80), 4)]
 EPS64 = np.finfo(np.float64).eps
