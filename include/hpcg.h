@@ -81,10 +81,11 @@ typedef struct {
                        smoother, no persistent kernel, grids up to 384 points along x) the level
                        vectors z are kept as 64-bit integer mantissas with one exponent per x-line,
                        so colour steps add exactly without converting each value they load; each
-                       new value is rounded once to about FP64 precision of its line (53 bits for
-                       values of the line's typical size, an absolute 2^-56 of its largest), and
-                       non-finite values end as NaN; r and the result z stay FP64.  0: the FP64
-                       V-cycle keeps z in FP64 */
+                       new value is rounded once, at an absolute 2^-56 of the largest term of its
+                       colour step (its line's and the neighbouring lines' values: 53 bits for
+                       values of the line's typical size, zero for values far below their
+                       neighbourhood's), and non-finite values end as NaN; r and the result z
+                       stay FP64.  0: the FP64 V-cycle keeps z in FP64 */
   int cluster_tail; /* 1: with block_fp, the levels of at most 32768 rows whose x-lines fit 64
                        points run in one launch of a 16-block thread-block cluster, runs separated
                        by the cluster barrier instead of kernel boundaries (same bits as one launch
